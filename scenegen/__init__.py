@@ -1,0 +1,22 @@
+"""Seeded synthetic inputs shared by the CUDA path and the oracle.
+
+This package only *generates inputs*: triangle meshes, per-triangle and
+per-instance materials, camera and instance keyframes, and environment-map
+texels.  It holds none of the method's arithmetic (no ray tracing, no
+statistics, no sampling of paths).  Every function is deterministic in its
+`seed` argument.
+"""
+from .procedural import (  # noqa: F401
+    Scene,
+    Workload,
+    WORKLOADS,
+    cornell_box,
+    empty_env,
+    furnace_sphere,
+    icosphere_field,
+    plane_under_env,
+    sky_texture,
+    static_variant,
+    terrain_with_boxes,
+    workload,
+)
