@@ -1,0 +1,207 @@
+/*
+ * mcev.h -- C ABI of the GB300 event-camera renderer.
+ *
+ * The library renders events the way "Monte Carlo Path Tracing and
+ * Statistical Event Detection for Event Camera Simulation" (arXiv 2408.07996)
+ * describes: per pixel it path-traces log luminance samples at two times,
+ * keeps their running mean and variance, runs a one-tailed Student t-test of
+ * whether the log-brightness gap is below the event threshold (Sec. 3.2,
+ * Eq. 5), re-queues only the undecided pixels for another batch of paths
+ * (Sec. 3.3) and emits an event with its polarity where the gap exceeds the
+ * threshold (Alg. 1, Eq. 1).
+ *
+ * Conventions shared by every entry point:
+ *  - Every call returns an mcev_status and never aborts or throws.  On an
+ *    error the message is available from mcev_last_error(ctx).
+ *  - "device" pointers are CUDA device pointers on the context's device;
+ *    "host" pointers are ordinary host memory.  Caller-owned buffers stay
+ *    owned by the caller; the library copies what it needs.
+ *  - All GPU work runs on the context's stream (mcev_set_stream; default:
+ *    the legacy default stream).  Calls are stream-ordered; a call that
+ *    returns host results synchronises the stream first.
+ *  - Pixels are indexed p = y * width + x, with y = 0 the top image row.
+ *  - Not thread-safe per context: one host thread drives a context at a time.
+ */
+#ifndef MCEV_H
+#define MCEV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mcev_ctx mcev_ctx;
+
+typedef enum {
+    MCEV_OK = 0,
+    MCEV_ERR_ARG = -1,      /* invalid argument (null, out of range, wrong size) */
+    MCEV_ERR_CUDA = -2,     /* a CUDA runtime call failed; see mcev_last_error */
+    MCEV_ERR_OOM = -3,      /* device or host allocation failed */
+    MCEV_ERR_TIMEOUT = -4,  /* reserved: a bounded device wait gave up */
+    MCEV_ERR_STATE = -5,    /* call out of order (e.g. render before scene upload) */
+    MCEV_ERR_NUMERIC = -6   /* reserved for numeric failures surfaced as errors */
+} mcev_status;
+
+/* Detector variants (Sec. 3.2 and its discussion; Sec. 4 baseline). */
+enum {
+    MCEV_ONE_TAILED = 0,    /* the paper's method: stop iff F_{n-1}(t) < alpha */
+    MCEV_TWO_TAILED = 1,    /* ablation: stop iff either tail is below alpha/2 */
+    MCEV_MEAN_ONLY = 2,     /* ablation: stop iff |mu_b - mu_a| < C */
+    MCEV_UNIFORM = 3        /* baseline: every pixel to spp_max, same event rule */
+};
+/* Standard error of Eq. 5: the paper's sqrt((s_a^2 + s_b^2) / n_b), or Welch's
+ * sqrt(s_a^2 / n_a + s_b^2 / n_b). */
+enum { MCEV_SE_PAPER = 0, MCEV_SE_WELCH = 1 };
+
+/* Scene description; every pointer is HOST memory and is copied.
+ * Triangles index a shared vertex pool; a mesh is a contiguous triangle
+ * range; an instance places a mesh with a row-major 3x4 object-to-world
+ * affine matrix per keyframe (linearly interpolated between keyframes,
+ * clamped outside).  Materials: type 0 Lambertian (albedo), 1 GGX
+ * reflector (albedo = Schlick normal-incidence reflectance, rough = GGX
+ * alpha).  emit > 0 makes a triangle a one-sided emitter on the side of its
+ * winding normal (v1-v0)x(v2-v0); such triangles are also sampled by NEE.
+ * env: [env_h][env_w] latitude-longitude scalar radiance, row 0 at +y,
+ * azimuth measured from +x towards +z; NULL for a black background. */
+typedef struct {
+    int64_t n_vertices;
+    const float* vertices;       /* [n_vertices][3] */
+    int64_t n_triangles;
+    const int32_t* triangles;    /* [n_triangles][3] vertex indices */
+    const int32_t* tri_material; /* [n_triangles] */
+    int32_t n_meshes;
+    const int32_t* mesh_ranges;  /* [n_meshes][2] = (first triangle, count) */
+    int32_t n_instances;
+    const int32_t* inst_mesh;     /* [n_instances] */
+    const int32_t* inst_material; /* [n_instances] override material id, or -1 */
+    int32_t n_keys;
+    const double* key_times;      /* [n_keys], strictly increasing */
+    const double* inst_xform;     /* [n_keys][n_instances][12] */
+    const double* cam_eye;        /* [n_keys][3] */
+    const double* cam_target;     /* [n_keys][3] */
+    const double* cam_up;         /* [n_keys][3] */
+    double fov_deg;               /* full field of view across the shorter image axis */
+    int32_t n_materials;
+    const int32_t* mat_type;      /* [n_materials] */
+    const float* mat_albedo;      /* [n_materials] */
+    const float* mat_rough;       /* [n_materials] */
+    const float* mat_emit;        /* [n_materials] */
+    int32_t env_w, env_h;
+    const float* env;             /* [env_h][env_w] or NULL */
+} mcev_scene_desc;
+
+/* Render settings (mcev_set_params). */
+typedef struct {
+    float eps;          /* dark level: each path contributes y = ln(L + eps) (Sec. 3.1) */
+    float t_min;        /* ray epsilon in scene units (self-intersection offset) */
+    int32_t max_depth;  /* scattering vertices with NEE + BSDF sampling (pbrt-v4 maxdepth) */
+    int32_t nee;        /* 1: next-event estimation at every vertex */
+    int32_t mis;        /* 1: power-heuristic MIS between NEE and BSDF sampling */
+    int32_t spp_min;    /* samples before the first t-test (Sec. 3.3: 256); >= 2 */
+    int32_t variant;    /* MCEV_ONE_TAILED ... MCEV_UNIFORM */
+    int32_t se_mode;    /* MCEV_SE_PAPER or MCEV_SE_WELCH */
+    uint64_t seed;      /* Philox key seed */
+    int64_t wavefront;  /* max paths in flight per chunk; 0 = library default */
+} mcev_params;
+
+/* Per-call counters (mcev_render_events, optional). */
+typedef struct {
+    int64_t paths;          /* path samples traced for the t1 frame */
+    int64_t ref_paths;      /* path samples traced for a t0 reference frame (0 if reused) */
+    int32_t rounds;         /* batch rounds at t1 */
+    int32_t kernel_launches;/* kernels launched by this call */
+    int64_t events_pos, events_neg;
+    int64_t pixels_at_cap;  /* pixels that used spp_max samples */
+    int64_t nonfinite;      /* path values that were not finite and counted as 0 */
+    double gpu_ms;          /* device time of the call (CUDA events) */
+} mcev_stats;
+
+/* Creates a context on CUDA device `device` for width x height images.
+ * *out receives the context (NULL on failure).  Errors: ARG, CUDA, OOM. */
+mcev_status mcev_create(mcev_ctx** out, int device, int32_t width, int32_t height);
+
+/* Frees every resource of the context (NULL is a no-op). */
+void mcev_destroy(mcev_ctx* ctx);
+
+/* Last error message of the context ("" when none); valid until the next call. */
+const char* mcev_last_error(const mcev_ctx* ctx);
+
+/* Uses `stream` (a cudaStream_t, e.g. torch's current stream) for all later
+ * GPU work of this context; NULL selects the legacy default stream. */
+mcev_status mcev_set_stream(mcev_ctx* ctx, void* stream);
+
+/* Routes the context's device allocations through alloc/free (e.g. a
+ * framework's caching allocator).  alloc returns NULL on failure, which
+ * the library reports as MCEV_ERR_OOM.  Must be called before
+ * mcev_scene_upload; NULL restores cudaMalloc/cudaFree. */
+typedef void* (*mcev_alloc_fn)(size_t bytes, void* user);
+typedef void (*mcev_free_fn)(void* ptr, void* user);
+mcev_status mcev_set_allocator(mcev_ctx* ctx, mcev_alloc_fn alloc, mcev_free_fn free_fn, void* user);
+
+/* Copies the scene to the device (see mcev_scene_desc) and builds one
+ * bounding volume hierarchy per mesh with default settings.  Invalidates
+ * the reference state.  Errors: ARG (bad index, size or key order), OOM, CUDA. */
+mcev_status mcev_scene_upload(mcev_ctx* ctx, const mcev_scene_desc* desc);
+
+/* Rebuilds the per-mesh BVHs with a binned surface-area heuristic of
+ * `sah_bins` bins (4..256) and leaves of at most `max_leaf` (1..16)
+ * triangles.  Errors: ARG, STATE (no scene), OOM, CUDA. */
+mcev_status mcev_build_bvh(mcev_ctx* ctx, int32_t sah_bins, int32_t max_leaf);
+
+/* Sets render settings (see mcev_params).  Errors: ARG. */
+mcev_status mcev_set_params(mcev_ctx* ctx, const mcev_params* params);
+
+/* First frame of Alg. 1: renders every pixel at time t0 with spp samples and
+ * stores (count, mean, M2) of ln(L + eps) as the reference state.  Errors:
+ * ARG, STATE, OOM, CUDA. */
+mcev_status mcev_render_reference(mcev_ctx* ctx, double t0, int32_t spp);
+
+/* One frame of Alg. 1 for the pair (t0, t1).  If the reference state is not
+ * valid or was last set for a time other than t0, the reference is first
+ * rendered at t0 with spp_max samples.  Then every pixel is sampled at t1
+ * in a first batch of params.spp_min samples and further batches of
+ * spp_batch, the t-test (Eq. 5 with the chosen variant and standard error)
+ * deciding after each batch whether the pixel stops, up to spp_max.  A
+ * decided pixel with |mean_t1 - mean_ref| > C gets event sign(gap) and its
+ * statistics become the new reference (Alg. 1); the reference time becomes t1.
+ *   events_out : device int8 [H*W], required: -1, 0, +1 per pixel
+ *   spp_out    : device int32 [H*W] or NULL: samples used per pixel
+ *   mean_out   : device float [H*W] or NULL: mean ln(L + eps) at t1
+ *   stats_out  : host or NULL; when non-NULL the call synchronises and fills it
+ * Sample k of pixel p at time t uses the same random numbers in every mode,
+ * so adaptive samples are a prefix of the uniform ones.
+ * Errors: ARG (C < 0, alpha outside (0,1), spp_batch < 1, spp_max < spp_min),
+ * STATE, OOM, CUDA. */
+mcev_status mcev_render_events(mcev_ctx* ctx, double t0, double t1, float C, float alpha,
+                               int32_t spp_batch, int32_t spp_max, int8_t* events_out,
+                               int32_t* spp_out, float* mean_out, mcev_stats* stats_out);
+
+/* tracePaths(q, s, N) of Alg. 1: path-traced radiance of samples
+ * k0 .. k0+count-1 of each listed pixel at time t.
+ *   pixels : device int32 [n_pix], values in [0, H*W)
+ *   L_out  : device float [n_pix][count]
+ *   sig_out: device uint32 [n_pix][count] or NULL: FNV-1a hash of every
+ *            discrete decision along the path (hit instance/triangle ids,
+ *            environment texel, emission, NEE, visibility and sampling flags)
+ * Errors: ARG, STATE, OOM, CUDA. */
+mcev_status mcev_trace_samples(mcev_ctx* ctx, double t, const int32_t* pixels, int64_t n_pix,
+                               int64_t k0, int32_t count, float* L_out, uint32_t* sig_out);
+
+/* Size in bytes of the reference-state blob: a 16-byte header (double
+ * reference time, int32 valid flag, int32 pixel count) followed by int32
+ * n[H*W], float mean[H*W], float M2[H*W]. */
+size_t mcev_state_bytes(const mcev_ctx* ctx);
+
+/* Copies the reference state (checkpoint) into a device buffer of
+ * mcev_state_bytes() bytes; mcev_set_state restores it (resume).  The state
+ * plus the reference time is all Alg. 1 carries between frames.
+ * Errors: ARG (NULL or wrong size), CUDA. */
+mcev_status mcev_get_state(mcev_ctx* ctx, void* dev_buf, size_t bytes);
+mcev_status mcev_set_state(mcev_ctx* ctx, const void* dev_buf, size_t bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

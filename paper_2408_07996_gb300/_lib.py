@@ -1,0 +1,115 @@
+"""ctypes declarations of the C ABI in include/mcev.h.
+
+Loads the in-tree `_build/libmcev.so` (building it with nvcc when it is
+missing or older than its sources) and fails loudly if that is impossible:
+there is no CPU fallback."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+from . import build as _build
+
+MCEV_OK = 0
+STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_CUDA", -3: "ERR_OOM", -4: "ERR_TIMEOUT", -5: "ERR_STATE",
+          -6: "ERR_NUMERIC"}
+
+ONE_TAILED, TWO_TAILED, MEAN_ONLY, UNIFORM = 0, 1, 2, 3
+SE_PAPER, SE_WELCH = 0, 1
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+class SceneDesc(C.Structure):
+    _fields_ = [
+        ("n_vertices", C.c_int64), ("vertices", C.c_void_p),
+        ("n_triangles", C.c_int64), ("triangles", C.c_void_p), ("tri_material", C.c_void_p),
+        ("n_meshes", C.c_int32), ("mesh_ranges", C.c_void_p),
+        ("n_instances", C.c_int32), ("inst_mesh", C.c_void_p), ("inst_material", C.c_void_p),
+        ("n_keys", C.c_int32), ("key_times", C.c_void_p), ("inst_xform", C.c_void_p),
+        ("cam_eye", C.c_void_p), ("cam_target", C.c_void_p), ("cam_up", C.c_void_p),
+        ("fov_deg", C.c_double),
+        ("n_materials", C.c_int32), ("mat_type", C.c_void_p), ("mat_albedo", C.c_void_p),
+        ("mat_rough", C.c_void_p), ("mat_emit", C.c_void_p),
+        ("env_w", C.c_int32), ("env_h", C.c_int32), ("env", C.c_void_p),
+    ]
+
+
+class Params(C.Structure):
+    _fields_ = [
+        ("eps", C.c_float), ("t_min", C.c_float), ("max_depth", C.c_int32), ("nee", C.c_int32),
+        ("mis", C.c_int32), ("spp_min", C.c_int32), ("variant", C.c_int32), ("se_mode", C.c_int32),
+        ("seed", C.c_uint64), ("wavefront", C.c_int64),
+    ]
+
+
+class Stats(C.Structure):
+    _fields_ = [
+        ("paths", C.c_int64), ("ref_paths", C.c_int64), ("rounds", C.c_int32),
+        ("kernel_launches", C.c_int32), ("events_pos", C.c_int64), ("events_neg", C.c_int64),
+        ("pixels_at_cap", C.c_int64), ("nonfinite", C.c_int64), ("gpu_ms", C.c_double),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+# every symbol include/mcev.h declares, with its ctypes signature
+SIGNATURES = {
+    "mcev_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int32, C.c_int32]),
+    "mcev_destroy": (None, [C.c_void_p]),
+    "mcev_last_error": (C.c_char_p, [C.c_void_p]),
+    "mcev_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "mcev_set_allocator": (C.c_int, [C.c_void_p, ALLOC_FN, FREE_FN, C.c_void_p]),
+    "mcev_scene_upload": (C.c_int, [C.c_void_p, C.POINTER(SceneDesc)]),
+    "mcev_build_bvh": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32]),
+    "mcev_set_params": (C.c_int, [C.c_void_p, C.POINTER(Params)]),
+    "mcev_render_reference": (C.c_int, [C.c_void_p, C.c_double, C.c_int32]),
+    "mcev_render_events": (C.c_int, [C.c_void_p, C.c_double, C.c_double, C.c_float, C.c_float, C.c_int32,
+                                     C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(Stats)]),
+    "mcev_trace_samples": (C.c_int, [C.c_void_p, C.c_double, C.c_void_p, C.c_int64, C.c_int64, C.c_int32,
+                                     C.c_void_p, C.c_void_p]),
+    "mcev_state_bytes": (C.c_size_t, [C.c_void_p]),
+    "mcev_get_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
+    "mcev_set_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
+}
+
+_lib = None
+_lock = threading.Lock()
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_needed: bool = True):
+    """The loaded libmcev.so (raises if it cannot be built or loaded)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if build_if_needed:
+                _build.build()
+            if not os.path.exists(_build.LIB):
+                raise ImportError(f"CUDA library {_build.LIB} is missing; run __graft_entry__.build()")
+            lib = C.CDLL(_build.LIB)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+class McevError(RuntimeError):
+    pass
+
+
+def check(status: int, ctx=None, what: str = "") -> None:
+    if status != MCEV_OK:
+        msg = ""
+        if ctx:
+            raw = load().mcev_last_error(ctx)
+            msg = raw.decode(errors="replace") if raw else ""
+        raise McevError(f"{what}: {STATUS.get(status, status)} {msg}".strip())

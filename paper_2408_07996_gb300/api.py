@@ -1,0 +1,207 @@
+"""Python face of the C ABI: argument marshalling only.
+
+PyTorch supplies device memory (through its caching allocator, installed as
+the library's allocator) and the CUDA stream; every step of the method runs
+in the library's kernels."""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+
+def _ptr(a: np.ndarray | None):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _tptr(t: torch.Tensor | None):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+@dataclass
+class RenderSettings:
+    eps: float = 1e-3
+    t_min: float = 1e-4
+    max_depth: int = 4
+    nee: int = 1
+    mis: int = 1
+    spp_min: int = 16
+    variant: int = L.ONE_TAILED
+    se_mode: int = L.SE_PAPER
+    seed: int = 20240815
+    wavefront: int = 0
+
+
+class Renderer:
+    """One rendering context (scene, BVH, per-pixel reference state) on one GPU.
+
+    Mirrors include/mcev.h: `upload`, `build_bvh`, `set_params`,
+    `render_reference`, `render_events`, `trace_samples`, `get_state`,
+    `set_state`."""
+
+    def __init__(self, width: int, height: int, device: int = 0, use_torch_allocator: bool = True):
+        if not torch.cuda.is_available():
+            raise RuntimeError("mcev needs a CUDA device; there is no CPU path")
+        self.lib = L.load()
+        self.width, self.height = int(width), int(height)
+        self.device = torch.device("cuda", device)
+        h = C.c_void_p()
+        L.check(self.lib.mcev_create(C.byref(h), device, self.width, self.height), None, "mcev_create")
+        self.ctx = h
+        self._keep = []
+        if use_torch_allocator:
+            dev = device
+
+            def _alloc(nbytes, user):
+                try:
+                    return torch.cuda.caching_allocator_alloc(int(nbytes), dev,
+                                                              torch.cuda.current_stream(dev).cuda_stream)
+                except Exception:  # reported to the library as NULL -> MCEV_ERR_OOM
+                    return None
+
+            def _free(ptr, user):
+                torch.cuda.caching_allocator_delete(ptr)
+
+            self._alloc_cb = L.ALLOC_FN(_alloc)
+            self._free_cb = L.FREE_FN(_free)
+            L.check(self.lib.mcev_set_allocator(self.ctx, self._alloc_cb, self._free_cb, None), self.ctx,
+                    "mcev_set_allocator")
+        self.set_stream(torch.cuda.current_stream(self.device))
+        self.settings = RenderSettings()
+
+    # ------------------------------------------------------------ lifetime
+    def close(self):
+        if getattr(self, "ctx", None):
+            torch.cuda.synchronize(self.device)
+            self.lib.mcev_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ------------------------------------------------------------ setup
+    def set_stream(self, stream: torch.cuda.Stream):
+        self.stream = stream
+        L.check(self.lib.mcev_set_stream(self.ctx, C.c_void_p(stream.cuda_stream)), self.ctx, "mcev_set_stream")
+
+    def upload(self, scene) -> None:
+        """Copies a `scenegen.Scene`-shaped object (host arrays) to the device."""
+        arrs = dict(
+            vertices=np.ascontiguousarray(scene.vertices, np.float32),
+            triangles=np.ascontiguousarray(scene.triangles, np.int32),
+            tri_material=np.ascontiguousarray(scene.tri_material, np.int32),
+            mesh_ranges=np.ascontiguousarray(scene.mesh_ranges, np.int32),
+            inst_mesh=np.ascontiguousarray(scene.inst_mesh, np.int32),
+            inst_material=np.ascontiguousarray(scene.inst_material, np.int32),
+            key_times=np.ascontiguousarray(scene.key_times, np.float64),
+            inst_xform=np.ascontiguousarray(scene.inst_xform, np.float64),
+            cam_eye=np.ascontiguousarray(scene.cam_eye, np.float64),
+            cam_target=np.ascontiguousarray(scene.cam_target, np.float64),
+            cam_up=np.ascontiguousarray(scene.cam_up, np.float64),
+            mat_type=np.ascontiguousarray(scene.mat_type, np.int32),
+            mat_albedo=np.ascontiguousarray(scene.mat_albedo, np.float32),
+            mat_rough=np.ascontiguousarray(scene.mat_rough, np.float32),
+            mat_emit=np.ascontiguousarray(scene.mat_emit, np.float32),
+        )
+        env = None if scene.env is None else np.ascontiguousarray(scene.env, np.float32)
+        d = L.SceneDesc(
+            n_vertices=arrs["vertices"].shape[0], vertices=_ptr(arrs["vertices"]),
+            n_triangles=arrs["triangles"].shape[0], triangles=_ptr(arrs["triangles"]),
+            tri_material=_ptr(arrs["tri_material"]),
+            n_meshes=arrs["mesh_ranges"].shape[0], mesh_ranges=_ptr(arrs["mesh_ranges"]),
+            n_instances=arrs["inst_mesh"].shape[0], inst_mesh=_ptr(arrs["inst_mesh"]),
+            inst_material=_ptr(arrs["inst_material"]),
+            n_keys=arrs["key_times"].shape[0], key_times=_ptr(arrs["key_times"]),
+            inst_xform=_ptr(arrs["inst_xform"]), cam_eye=_ptr(arrs["cam_eye"]),
+            cam_target=_ptr(arrs["cam_target"]), cam_up=_ptr(arrs["cam_up"]), fov_deg=float(scene.fov_deg),
+            n_materials=arrs["mat_type"].shape[0], mat_type=_ptr(arrs["mat_type"]),
+            mat_albedo=_ptr(arrs["mat_albedo"]), mat_rough=_ptr(arrs["mat_rough"]),
+            mat_emit=_ptr(arrs["mat_emit"]),
+            env_w=0 if env is None else env.shape[1], env_h=0 if env is None else env.shape[0], env=_ptr(env))
+        L.check(self.lib.mcev_scene_upload(self.ctx, C.byref(d)), self.ctx, "mcev_scene_upload")
+
+    def build_bvh(self, sah_bins: int = 32, max_leaf: int = 4) -> None:
+        L.check(self.lib.mcev_build_bvh(self.ctx, sah_bins, max_leaf), self.ctx, "mcev_build_bvh")
+
+    def set_params(self, **kw) -> RenderSettings:
+        for k, v in kw.items():
+            if not hasattr(self.settings, k):
+                raise KeyError(k)
+            setattr(self.settings, k, v)
+        s = self.settings
+        p = L.Params(eps=s.eps, t_min=s.t_min, max_depth=s.max_depth, nee=s.nee, mis=s.mis,
+                     spp_min=s.spp_min, variant=s.variant, se_mode=s.se_mode, seed=s.seed,
+                     wavefront=s.wavefront)
+        L.check(self.lib.mcev_set_params(self.ctx, C.byref(p)), self.ctx, "mcev_set_params")
+        return s
+
+    def configure(self, w) -> None:
+        """Settings of a `scenegen.Workload`."""
+        self.set_params(eps=w.eps, t_min=w.t_min, max_depth=w.max_depth, nee=w.nee, mis=w.mis,
+                        spp_min=w.spp_min, seed=w.seed)
+
+    # ------------------------------------------------------------ rendering
+    def render_reference(self, t0: float, spp: int) -> None:
+        L.check(self.lib.mcev_render_reference(self.ctx, float(t0), int(spp)), self.ctx, "mcev_render_reference")
+
+    def render_events(self, t0: float, t1: float, C_: float, alpha: float, spp_batch: int, spp_max: int,
+                      out: dict | None = None, stats: bool = True) -> dict:
+        """One Alg. 1 frame; returns events (int8 [H,W]), spp (int32), mean (float32)."""
+        H, W = self.height, self.width
+        if out is None:
+            out = dict(events=torch.empty((H, W), dtype=torch.int8, device=self.device),
+                       spp=torch.empty((H, W), dtype=torch.int32, device=self.device),
+                       mean=torch.empty((H, W), dtype=torch.float32, device=self.device))
+        st = L.Stats()
+        L.check(self.lib.mcev_render_events(self.ctx, float(t0), float(t1), float(C_), float(alpha), int(spp_batch),
+                                            int(spp_max), _tptr(out["events"]), _tptr(out.get("spp")),
+                                            _tptr(out.get("mean")), C.byref(st) if stats else None),
+                self.ctx, "mcev_render_events")
+        if stats:
+            out["stats"] = st.as_dict()
+        return out
+
+    def trace_samples(self, t: float, pixels: torch.Tensor, k0: int, count: int, want_sig: bool = True):
+        """tracePaths: per-sample radiance [n, count] (and decision signatures)."""
+        pixels = pixels.to(device=self.device, dtype=torch.int32).contiguous()
+        n = pixels.numel()
+        Lo = torch.empty((n, count), dtype=torch.float32, device=self.device)
+        sig = torch.empty((n, count), dtype=torch.int32, device=self.device) if want_sig else None
+        L.check(self.lib.mcev_trace_samples(self.ctx, float(t), _tptr(pixels), n, int(k0), int(count), _tptr(Lo),
+                                            _tptr(sig)), self.ctx, "mcev_trace_samples")
+        return Lo, sig
+
+    def state_bytes(self) -> int:
+        return int(self.lib.mcev_state_bytes(self.ctx))
+
+    def get_state(self) -> torch.Tensor:
+        buf = torch.empty(self.state_bytes(), dtype=torch.uint8, device=self.device)
+        L.check(self.lib.mcev_get_state(self.ctx, _tptr(buf), buf.numel()), self.ctx, "mcev_get_state")
+        return buf
+
+    def set_state(self, buf: torch.Tensor) -> None:
+        buf = buf.to(self.device).contiguous()
+        L.check(self.lib.mcev_set_state(self.ctx, _tptr(buf), buf.numel()), self.ctx, "mcev_set_state")
+
+    def reference_arrays(self):
+        """Reference state as (n, mean, M2) tensors [H, W] (views of a state copy)."""
+        b = self.get_state()
+        n = self.width * self.height
+        body = b[16:]
+        cnt = body[: 4 * n].view(torch.int32).view(self.height, self.width)
+        mean = body[4 * n: 8 * n].view(torch.float32).view(self.height, self.width)
+        m2 = body[8 * n: 12 * n].view(torch.float32).view(self.height, self.width)
+        return cnt, mean, m2

@@ -1,0 +1,977 @@
+// api.cpp -- the C ABI of include/mcev.h: context, scene upload, per-frame
+// setup and the host loop of Alg. 1 (rounds of batches over a device queue of
+// undecided pixels, each round split into wavefront chunks).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+#include <map>
+#include <new>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/mcev.h"
+#include "bvh.h"
+#include "kernels.h"
+#include "layout.h"
+#include "tdist.h"
+
+using namespace mcev;
+
+namespace {
+
+struct DevBuf {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+};
+
+struct MeshInfo {
+    int64_t first_tri, n_tri;   // in the uploaded triangle list
+    int64_t tri_offset;         // first slot in the device triangle array
+    int root;                   // BLAS root node (global index)
+    float lo[3], hi[3];         // object-space bounds (root box)
+};
+
+struct Frame {
+    DevFrame dev{};
+    DevBuf buf;                 // TLAS nodes | instances | lights
+    double time = 0.0;
+    bool valid = false;
+};
+
+}  // namespace
+
+struct mcev_ctx {
+    int device = 0;
+    int sms = 152;
+    int32_t W = 0, H = 0;
+    cudaStream_t stream = nullptr;
+    mcev_alloc_fn alloc = nullptr;
+    mcev_free_fn free_fn = nullptr;
+    void* alloc_user = nullptr;
+    std::string err;
+    mcev_params params{};
+    int launches = 0;
+
+    // host copy of the scene (needed per frame)
+    bool have_scene = false;
+    int32_t n_inst = 0, n_keys = 0, n_mats = 0;
+    std::vector<float> vtx;                 // [tri][9] object space
+    std::vector<int32_t> tri_mat;
+    std::vector<MeshInfo> meshes;
+    std::vector<int32_t> inst_mesh, inst_mat;
+    std::vector<double> key_t, key_xf, cam_eye, cam_tgt, cam_up;
+    double fov_deg = 45.0;
+    std::vector<int32_t> mat_type;
+    std::vector<float> mat_alb, mat_rough, mat_emit;
+    std::vector<std::pair<int32_t, int64_t>> emitters;  // (instance, triangle)
+    int32_t env_w = 0, env_h = 0;
+    std::vector<float> env;
+    bool env_ok = false;
+    int sah_bins = 32, max_leaf = 4;
+    int bvh_depth = 0;
+
+    // device scene
+    DevBuf d_nodes, d_tris, d_mats, d_env, d_marg, d_cond, d_tpdf;
+    DevScene dsc{};
+    Frame frames[2];
+
+    // wavefront + per-pixel state
+    DevBuf d_wave;
+    Wave wave{};
+    DevBuf d_counters;  // 16 int32: wave counters + error flag
+    DevBuf d_pix;       // queues + cur + ref
+    int32_t* queue[2] = {nullptr, nullptr};
+    PixStats cur{}, ref{};
+    bool ref_valid = false;
+    double ref_time = 0.0;
+
+    // t critical values
+    DevBuf d_tcrit;
+    std::tuple<float, int, int, int, int> tcrit_key{-1.0f, -1, -1, -1, -1};
+
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+namespace {
+
+mcev_status fail(mcev_ctx* c, mcev_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    return s;
+}
+
+#define CU(call)                                                                                   \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess)                                                                     \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? MCEV_ERR_OOM : MCEV_ERR_CUDA,       \
+                        "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+#define ST(call)                                   \
+    do {                                           \
+        mcev_status s_ = (call);                   \
+        if (s_ != MCEV_OK) return s_;              \
+    } while (0)
+
+mcev_status dev_alloc(mcev_ctx* ctx, DevBuf& b, size_t bytes) {
+    if (b.ptr && b.bytes >= bytes) return MCEV_OK;
+    if (b.ptr) {
+        if (ctx->alloc) ctx->free_fn(b.ptr, ctx->alloc_user);
+        else cudaFree(b.ptr);
+        b.ptr = nullptr;
+        b.bytes = 0;
+    }
+    if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) & ~size_t(255);
+    if (ctx->alloc) {
+        b.ptr = ctx->alloc(bytes, ctx->alloc_user);
+        if (!b.ptr) return fail(ctx, MCEV_ERR_OOM, "allocator returned NULL for %zu bytes", bytes);
+    } else {
+        cudaError_t e = cudaMalloc(&b.ptr, bytes);
+        if (e != cudaSuccess) {
+            b.ptr = nullptr;
+            cudaGetLastError();
+            return fail(ctx, MCEV_ERR_OOM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+        }
+    }
+    b.bytes = bytes;
+    return MCEV_OK;
+}
+
+void dev_free(mcev_ctx* ctx, DevBuf& b) {
+    if (!b.ptr) return;
+    if (ctx->alloc) ctx->free_fn(b.ptr, ctx->alloc_user);
+    else cudaFree(b.ptr);
+    b.ptr = nullptr;
+    b.bytes = 0;
+}
+
+mcev_status upload(mcev_ctx* ctx, DevBuf& b, const void* src, size_t bytes) {
+    ST(dev_alloc(ctx, b, bytes));
+    if (bytes) {
+        CU(cudaMemcpyAsync(b.ptr, src, bytes, cudaMemcpyHostToDevice, ctx->stream));
+        CU(cudaStreamSynchronize(ctx->stream));
+    }
+    return MCEV_OK;
+}
+
+// ---------------------------------------------------------------- affine helpers (FP64)
+void affine_inverse(const double* M, double* R) {
+    const double a = M[0], b = M[1], c = M[2], d = M[4], e = M[5], f = M[6], g = M[8], h = M[9], i = M[10];
+    const double A = e * i - f * h, B = -(d * i - f * g), Cc = d * h - e * g;
+    const double det = a * A + b * B + c * Cc;
+    const double id = 1.0 / det;
+    const double inv[9] = {A * id, -(b * i - c * h) * id, (b * f - c * e) * id,
+                           B * id, (a * i - c * g) * id,  -(a * f - c * d) * id,
+                           Cc * id, -(a * h - b * g) * id, (a * e - b * d) * id};
+    for (int r = 0; r < 3; ++r) {
+        R[4 * r + 0] = inv[3 * r + 0];
+        R[4 * r + 1] = inv[3 * r + 1];
+        R[4 * r + 2] = inv[3 * r + 2];
+        R[4 * r + 3] = -(inv[3 * r + 0] * M[3] + inv[3 * r + 1] * M[7] + inv[3 * r + 2] * M[11]);
+    }
+}
+
+void xf_point(const double* M, const double* p, double* o) {
+    for (int r = 0; r < 3; ++r) o[r] = M[4 * r] * p[0] + M[4 * r + 1] * p[1] + M[4 * r + 2] * p[2] + M[4 * r + 3];
+}
+
+void cross(const double* a, const double* b, double* o) {
+    o[0] = a[1] * b[2] - a[2] * b[1];
+    o[1] = a[2] * b[0] - a[0] * b[2];
+    o[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+double norm(const double* a) { return std::sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]); }
+
+uint32_t frame_key(double t) {
+    uint64_t b;
+    std::memcpy(&b, &t, sizeof b);
+    return (uint32_t)(b ^ (b >> 32));
+}
+
+// ---------------------------------------------------------------- scene build
+mcev_status build_blas(mcev_ctx* ctx) {
+    std::vector<Node> nodes;
+    std::vector<float4> tris;
+    tris.reserve(ctx->vtx.size() / 3);
+    int depth = 0;
+    for (auto& m : ctx->meshes) {
+        const int n = (int)m.n_tri;
+        std::vector<float> lo(3 * (size_t)n), hi(3 * (size_t)n), ce(3 * (size_t)n);
+        for (int i = 0; i < n; ++i) {
+            const float* v = &ctx->vtx[9 * (size_t)(m.first_tri + i)];
+            for (int a = 0; a < 3; ++a) {
+                lo[3 * i + a] = std::min(v[a], std::min(v[3 + a], v[6 + a]));
+                hi[3 * i + a] = std::max(v[a], std::max(v[3 + a], v[6 + a]));
+                ce[3 * i + a] = (float)(((double)v[a] + v[3 + a] + v[6 + a]) / 3.0);
+            }
+        }
+        BuiltBvh b = build_bvh(lo.data(), hi.data(), ce.data(), n, ctx->sah_bins, ctx->max_leaf);
+        depth = std::max(depth, b.depth);
+        const int node_off = (int)nodes.size();
+        m.tri_offset = (int64_t)tris.size() / 3;
+        m.root = node_off;
+        for (Node nd : b.nodes) {
+            if (nd.d.x >= 0) nd.d.x += node_off;
+            else nd.d.x = ~(int)(m.tri_offset + ~nd.d.x);
+            if (nd.d.y >= 0) nd.d.y += node_off;
+            else nd.d.y = ~(int)(m.tri_offset + ~nd.d.y);
+            nodes.push_back(nd);
+        }
+        for (int k = 0; k < 3; ++k) {
+            m.lo[k] = std::numeric_limits<float>::max();
+            m.hi[k] = -std::numeric_limits<float>::max();
+        }
+        for (int i = 0; i < n; ++i) {
+            const int64_t prim = m.first_tri + b.order[i];
+            const float* v = &ctx->vtx[9 * (size_t)prim];
+            float4 t0, t1, t2;
+            t0.x = v[0]; t0.y = v[1]; t0.z = v[2];
+            int pi = (int)prim, mi = ctx->tri_mat[prim];
+            std::memcpy(&t0.w, &pi, 4);
+            t1.x = v[3]; t1.y = v[4]; t1.z = v[5];
+            std::memcpy(&t1.w, &mi, 4);
+            t2.x = v[6]; t2.y = v[7]; t2.z = v[8]; t2.w = 0.0f;
+            tris.push_back(t0);
+            tris.push_back(t1);
+            tris.push_back(t2);
+            for (int a = 0; a < 3; ++a) {
+                m.lo[a] = std::min(m.lo[a], std::min(v[a], std::min(v[3 + a], v[6 + a])));
+                m.hi[a] = std::max(m.hi[a], std::max(v[a], std::max(v[3 + a], v[6 + a])));
+            }
+        }
+    }
+    if (depth + 16 > MCEV_STACK_HOST)
+        return fail(ctx, MCEV_ERR_ARG, "BVH depth %d exceeds the traversal stack", depth);
+    ctx->bvh_depth = depth;
+    ST(upload(ctx, ctx->d_nodes, nodes.data(), nodes.size() * sizeof(Node)));
+    ST(upload(ctx, ctx->d_tris, tris.data(), tris.size() * sizeof(float4)));
+    ctx->dsc.nodes = (const Node*)ctx->d_nodes.ptr;
+    ctx->dsc.tris = (const float4*)ctx->d_tris.ptr;
+    for (auto& f : ctx->frames) f.valid = false;
+    return MCEV_OK;
+}
+
+// Environment tables.  Row weights sum_j L_ij sin(pi (i + 1/2) / H), column
+// weights L_ij; prefix sums in FP64 in index order, divided by the total and
+// rounded to FP32, so the discrete texel choice is made on FP32 numbers.
+mcev_status build_env(mcev_ctx* ctx) {
+    const int W = ctx->env_w, H = ctx->env_h;
+    std::vector<float> marg(H + 1), cond((size_t)H * (W + 1)), tpdf((size_t)W * H);
+    std::vector<double> raw(W + 1), mraw(H + 1), rowsin(H);
+    mraw[0] = 0.0;
+    for (int i = 0; i < H; ++i) {
+        const double sin_t = std::sin(M_PI * (i + 0.5) / H);
+        rowsin[i] = sin_t;
+        raw[0] = 0.0;
+        for (int j = 0; j < W; ++j) raw[j + 1] = raw[j] + (double)ctx->env[(size_t)i * W + j];
+        const double rowsum = raw[W];
+        float* c = &cond[(size_t)i * (W + 1)];
+        for (int j = 0; j < W; ++j) c[j] = rowsum > 0.0 ? (float)(raw[j] / rowsum) : (float)((double)j / W);
+        c[W] = 1.0f;
+        mraw[i + 1] = mraw[i] + rowsum * sin_t;
+    }
+    const double total = mraw[H];
+    for (int i = 0; i < H; ++i) marg[i] = total > 0.0 ? (float)(mraw[i] / total) : (float)((double)i / H);
+    marg[H] = 1.0f;
+    for (int i = 0; i < H; ++i)
+        for (int j = 0; j < W; ++j)
+            tpdf[(size_t)i * W + j] = total > 0.0 ? (float)((double)ctx->env[(size_t)i * W + j] * rowsin[i] / total *
+                                                            (double)W * (double)H / (2.0 * M_PI * M_PI))
+                                                  : 0.0f;
+    ctx->env_ok = total > 0.0;
+    ST(upload(ctx, ctx->d_env, ctx->env.data(), ctx->env.size() * sizeof(float)));
+    ST(upload(ctx, ctx->d_marg, marg.data(), marg.size() * sizeof(float)));
+    ST(upload(ctx, ctx->d_cond, cond.data(), cond.size() * sizeof(float)));
+    ST(upload(ctx, ctx->d_tpdf, tpdf.data(), tpdf.size() * sizeof(float)));
+    ctx->dsc.env = (const float*)ctx->d_env.ptr;
+    ctx->dsc.env_marg = (const float*)ctx->d_marg.ptr;
+    ctx->dsc.env_cond = (const float*)ctx->d_cond.ptr;
+    ctx->dsc.env_tpdf = (const float*)ctx->d_tpdf.ptr;
+    ctx->dsc.env_w = W;
+    ctx->dsc.env_h = H;
+    ctx->dsc.env_ok = ctx->env_ok ? 1 : 0;
+    ctx->dsc.has_env = 1;
+    return MCEV_OK;
+}
+
+// ---------------------------------------------------------------- per-frame state
+mcev_status frame_setup(mcev_ctx* ctx, double t, int slot) {
+    Frame& fr = ctx->frames[slot];
+    if (fr.valid && fr.time == t) return MCEV_OK;
+    const int ni = ctx->n_inst, nk = ctx->n_keys;
+    int k = 0;
+    double f = 0.0;
+    if (nk > 1) {
+        while (k + 1 < nk - 1 && ctx->key_t[k + 1] <= t) ++k;
+        f = (t - ctx->key_t[k]) / (ctx->key_t[k + 1] - ctx->key_t[k]);
+        f = std::min(1.0, std::max(0.0, f));
+    }
+    const int k1 = nk > 1 ? k + 1 : k;
+    auto lerp = [f](double a, double b) { return (1.0 - f) * a + f * b; };
+    std::vector<double> M((size_t)ni * 12), Mi((size_t)ni * 12);
+    std::vector<float> blo(3 * (size_t)ni), bhi(3 * (size_t)ni), bce(3 * (size_t)ni);
+    std::vector<float4> inst((size_t)ni * 7);
+    for (int i = 0; i < ni; ++i) {
+        const double* A = &ctx->key_xf[12 * ((size_t)k * ni + i)];
+        const double* B = &ctx->key_xf[12 * ((size_t)k1 * ni + i)];
+        double* m = &M[12 * (size_t)i];
+        for (int e = 0; e < 12; ++e) m[e] = lerp(A[e], B[e]);
+        double* mi = &Mi[12 * (size_t)i];
+        affine_inverse(m, mi);
+        const MeshInfo& mesh = ctx->meshes[ctx->inst_mesh[i]];
+        float lo[3] = {std::numeric_limits<float>::max(), std::numeric_limits<float>::max(),
+                       std::numeric_limits<float>::max()};
+        float hi[3] = {-lo[0], -lo[1], -lo[2]};
+        if (mesh.n_tri > 0) {
+            for (int c = 0; c < 8; ++c) {
+                const double q[3] = {(c & 1) ? mesh.hi[0] : mesh.lo[0], (c & 2) ? mesh.hi[1] : mesh.lo[1],
+                                     (c & 4) ? mesh.hi[2] : mesh.lo[2]};
+                double w[3];
+                xf_point(m, q, w);
+                for (int a = 0; a < 3; ++a) {
+                    // round outwards so the FP32 box contains the FP64 corners
+                    lo[a] = std::min(lo[a], std::nextafter((float)w[a], -INFINITY));
+                    hi[a] = std::max(hi[a], std::nextafter((float)w[a], INFINITY));
+                }
+            }
+        } else {
+            for (int a = 0; a < 3; ++a) lo[a] = hi[a] = 1e30f;
+        }
+        for (int a = 0; a < 3; ++a) {
+            blo[3 * i + a] = lo[a];
+            bhi[3 * i + a] = hi[a];
+            bce[3 * i + a] = 0.5f * (lo[a] + hi[a]);
+        }
+        for (int r = 0; r < 3; ++r) {
+            inst[7 * i + r] = make_float4((float)m[4 * r], (float)m[4 * r + 1], (float)m[4 * r + 2], (float)m[4 * r + 3]);
+            inst[7 * i + 3 + r] =
+                make_float4((float)mi[4 * r], (float)mi[4 * r + 1], (float)mi[4 * r + 2], (float)mi[4 * r + 3]);
+        }
+        int root = mesh.root, ovr = ctx->inst_mat[i];
+        float4 tail = make_float4(0, 0, 0, 0);
+        std::memcpy(&tail.x, &root, 4);
+        std::memcpy(&tail.y, &ovr, 4);
+        inst[7 * i + 6] = tail;
+    }
+    // TLAS over instance boxes, one instance per leaf; leaf ref = ~instance id
+    std::vector<Node> tlas;
+    if (ni > 1) {
+        BuiltBvh b = build_bvh(blo.data(), bhi.data(), bce.data(), ni, 16, 1);
+        tlas = b.nodes;
+        for (Node& nd : tlas) {
+            if (nd.d.x < 0 && nd.d.z > 0) nd.d.x = ~b.order[~nd.d.x];
+            if (nd.d.y < 0 && nd.d.w > 0) nd.d.y = ~b.order[~nd.d.y];
+        }
+        if (b.depth + ctx->bvh_depth + 8 > MCEV_STACK_HOST)
+            return fail(ctx, MCEV_ERR_ARG, "TLAS + BLAS depth exceeds the traversal stack");
+    }
+    // emitters in world space
+    std::vector<float4> lights(ctx->emitters.size() * 4);
+    for (size_t l = 0; l < ctx->emitters.size(); ++l) {
+        const int i = ctx->emitters[l].first;
+        const int64_t prim = ctx->emitters[l].second;
+        const double* m = &M[12 * (size_t)i];
+        const float* v = &ctx->vtx[9 * (size_t)prim];
+        double p[3][3];
+        for (int c = 0; c < 3; ++c) {
+            const double q[3] = {v[3 * c], v[3 * c + 1], v[3 * c + 2]};
+            xf_point(m, q, p[c]);
+        }
+        double e1[3], e2[3], cr[3];
+        for (int a = 0; a < 3; ++a) {
+            e1[a] = p[1][a] - p[0][a];
+            e2[a] = p[2][a] - p[0][a];
+        }
+        cross(e1, e2, cr);
+        const double len = norm(cr);
+        const int mat = ctx->inst_mat[i] >= 0 ? ctx->inst_mat[i] : ctx->tri_mat[prim];
+        lights[4 * l + 0] = make_float4((float)p[0][0], (float)p[0][1], (float)p[0][2], ctx->mat_emit[mat]);
+        lights[4 * l + 1] = make_float4((float)p[1][0], (float)p[1][1], (float)p[1][2], (float)(0.5 * len));
+        lights[4 * l + 2] = make_float4((float)p[2][0], (float)p[2][1], (float)p[2][2], 0.0f);
+        lights[4 * l + 3] = make_float4((float)(cr[0] / len), (float)(cr[1] / len), (float)(cr[2] / len), 0.0f);
+    }
+    const size_t nb_t = tlas.size() * sizeof(Node), nb_i = inst.size() * sizeof(float4),
+                 nb_l = lights.size() * sizeof(float4);
+    auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+    const size_t total = al(nb_t) + al(nb_i) + al(nb_l);
+    ST(dev_alloc(ctx, fr.buf, total));
+    std::vector<char> host(total, 0);
+    std::memcpy(host.data(), tlas.data(), nb_t);
+    std::memcpy(host.data() + al(nb_t), inst.data(), nb_i);
+    std::memcpy(host.data() + al(nb_t) + al(nb_i), lights.data(), nb_l);
+    // the stream may still be reading the slot from an earlier frame
+    CU(cudaStreamSynchronize(ctx->stream));
+    CU(cudaMemcpyAsync(fr.buf.ptr, host.data(), total, cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    char* base = (char*)fr.buf.ptr;
+    DevFrame& d = fr.dev;
+    d.tlas = (const Node*)base;
+    d.inst = (const float4*)(base + al(nb_t));
+    d.lights = (const float4*)(base + al(nb_t) + al(nb_i));
+    d.n_inst = ni;
+    d.n_lights = (int32_t)ctx->emitters.size();
+    d.tlas_is_leaf = ni <= 1 ? 1 : 0;
+    // camera (FP64 then rounded)
+    double eye[3], tgt[3], up[3];
+    for (int a = 0; a < 3; ++a) {
+        eye[a] = lerp(ctx->cam_eye[3 * k + a], ctx->cam_eye[3 * k1 + a]);
+        tgt[a] = lerp(ctx->cam_tgt[3 * k + a], ctx->cam_tgt[3 * k1 + a]);
+        up[a] = lerp(ctx->cam_up[3 * k + a], ctx->cam_up[3 * k1 + a]);
+    }
+    double fwd[3] = {tgt[0] - eye[0], tgt[1] - eye[1], tgt[2] - eye[2]};
+    const double fl = norm(fwd);
+    for (double& x : fwd) x /= fl;
+    double right[3], upv[3];
+    cross(fwd, up, right);
+    const double rl = norm(right);
+    for (double& x : right) x /= rl;
+    cross(right, fwd, upv);
+    const double th = std::tan(0.5 * ctx->fov_deg * M_PI / 180.0);
+    double sx, sy;
+    if (ctx->W >= ctx->H) {
+        sy = th;
+        sx = th * (double)ctx->W / (double)ctx->H;
+    } else {
+        sx = th;
+        sy = th * (double)ctx->H / (double)ctx->W;
+    }
+    for (int a = 0; a < 3; ++a) {
+        d.eye[a] = (float)eye[a];
+        d.fwd[a] = (float)fwd[a];
+        d.right[a] = (float)(right[a] * sx);
+        d.up[a] = (float)(upv[a] * sy);
+    }
+    d.key0 = (uint32_t)ctx->params.seed ^ frame_key(t);
+    d.key1 = (uint32_t)(ctx->params.seed >> 32);
+    const bool have_area = !ctx->emitters.empty();
+    d.p_env = ctx->env_ok ? (have_area ? 0.5f : 1.0f) : 0.0f;
+    d.p_area = have_area ? (ctx->env_ok ? 0.5f : 1.0f) : 0.0f;
+    fr.time = t;
+    fr.valid = true;
+    // the other slot must not alias this time's state
+    return MCEV_OK;
+}
+
+// ---------------------------------------------------------------- buffers
+mcev_status ensure_wave(mcev_ctx* ctx) {
+    const int64_t cap = ctx->params.wavefront > 0 ? ctx->params.wavefront : ((int64_t)1 << 23);
+    if (ctx->d_wave.ptr && ctx->wave.cap == cap) return MCEV_OK;
+    const size_t per = 4 * 3 + 4 * 2 + 8 + 16 * 2 * 2 + 16 + 16 * 2 + 4;
+    ST(dev_alloc(ctx, ctx->d_wave, (size_t)cap * per + 64 * 256));
+    char* p = (char*)ctx->d_wave.ptr;
+    auto take = [&](size_t bytes) {
+        char* r = p;
+        p += (bytes + 255) & ~size_t(255);
+        return r;
+    };
+    Wave& w = ctx->wave;
+    w.cap = cap;
+    w.ray_o[0] = (float4*)take(16 * cap);
+    w.ray_o[1] = (float4*)take(16 * cap);
+    w.ray_d[0] = (float4*)take(16 * cap);
+    w.ray_d[1] = (float4*)take(16 * cap);
+    w.hit = (float4*)take(16 * cap);
+    w.sh_o = (float4*)take(16 * cap);
+    w.sh_d = (float4*)take(16 * cap);
+    w.pix_k = (int2*)take(8 * cap);
+    w.beta = (float*)take(4 * cap);
+    w.L = (float*)take(4 * cap);
+    w.pdf_prev = (float*)take(4 * cap);
+    w.sig = (uint32_t*)take(4 * cap);
+    w.pflags = (uint32_t*)take(4 * cap);
+    w.sh_c = (float*)take(4 * cap);
+    if (!ctx->d_counters.ptr) {
+        ST(dev_alloc(ctx, ctx->d_counters, 64 * sizeof(int32_t)));
+        CU(cudaMemsetAsync(ctx->d_counters.ptr, 0, 64 * sizeof(int32_t), ctx->stream));
+    }
+    w.counters = (int32_t*)ctx->d_counters.ptr;
+    return MCEV_OK;
+}
+
+mcev_status ensure_pixels(mcev_ctx* ctx) {
+    if (ctx->d_pix.ptr) return MCEV_OK;
+    const size_t n = (size_t)ctx->W * ctx->H;
+    auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+    ST(dev_alloc(ctx, ctx->d_pix, 8 * al(4 * n)));
+    char* p = (char*)ctx->d_pix.ptr;
+    ctx->queue[0] = (int32_t*)p;
+    ctx->queue[1] = (int32_t*)(p + al(4 * n));
+    ctx->cur.n = (int32_t*)(p + 2 * al(4 * n));
+    ctx->cur.mean = (float*)(p + 3 * al(4 * n));
+    ctx->cur.m2 = (float*)(p + 4 * al(4 * n));
+    ctx->ref.n = (int32_t*)(p + 5 * al(4 * n));
+    ctx->ref.mean = (float*)(p + 6 * al(4 * n));
+    ctx->ref.m2 = (float*)(p + 7 * al(4 * n));
+    CU(cudaMemsetAsync(ctx->d_pix.ptr, 0, 8 * al(4 * n), ctx->stream));
+    return MCEV_OK;
+}
+
+mcev_status ensure_tcrit(mcev_ctx* ctx, float alpha, int variant, int spp_min, int spp_batch, int spp_max) {
+    auto key = std::make_tuple(alpha, variant, spp_min, spp_batch, spp_max);
+    if (ctx->d_tcrit.ptr && key == ctx->tcrit_key) return MCEV_OK;
+    std::vector<float> tab;
+    for (int n = spp_min; n < spp_max; n += spp_batch) {
+        const double p = variant == MCEV_TWO_TAILED ? 0.5 * (double)alpha : (double)alpha;
+        tab.push_back((float)t_quantile_int(p, n - 1));
+    }
+    if (tab.empty()) tab.push_back(0.0f);
+    ST(upload(ctx, ctx->d_tcrit, tab.data(), tab.size() * sizeof(float)));
+    ctx->tcrit_key = key;
+    return MCEV_OK;
+}
+
+DevParams dev_params(const mcev_ctx* ctx, bool want_sig) {
+    DevParams P;
+    P.width = ctx->W;
+    P.height = ctx->H;
+    P.max_depth = ctx->params.max_depth;
+    P.nee = ctx->params.nee;
+    P.mis = ctx->params.mis;
+    P.eps = ctx->params.eps;
+    P.t_min = ctx->params.t_min;
+    P.want_sig = want_sig ? 1 : 0;
+    return P;
+}
+
+#define LAUNCH(expr)                                                                                  \
+    do {                                                                                              \
+        cudaError_t e_ = (expr);                                                                      \
+        ++ctx->launches;                                                                              \
+        if (e_ != cudaSuccess)                                                                        \
+            return fail(ctx, MCEV_ERR_CUDA, "launch %s failed: %s", #expr, cudaGetErrorString(e_));   \
+    } while (0)
+
+// one chunk of n_paths = nj * spp_r paths through every bounce
+mcev_status trace_chunk(mcev_ctx* ctx, const Frame& fr, const DevParams& P, const int32_t* queue, int64_t j0,
+                        int32_t spp_r, int64_t k_base, int64_t n_paths) {
+    const Wave& w = ctx->wave;
+    int32_t* err = ctx->wave.counters + 15;
+    LAUNCH(launch_raygen(fr.dev, P, w, queue, j0, spp_r, k_base, n_paths, 0, ctx->sms, ctx->stream));
+    int cur = 0;
+    for (int depth = 0; depth <= P.max_depth; ++depth) {
+        LAUNCH(launch_extend(ctx->dsc, fr.dev, P.t_min, w, cur, n_paths, err, ctx->sms, ctx->stream));
+        LAUNCH(launch_shade(ctx->dsc, fr.dev, P, w, cur, n_paths, ctx->sms, ctx->stream));
+        if (depth < P.max_depth && P.nee)
+            LAUNCH(launch_shadow(ctx->dsc, fr.dev, P, w, n_paths, err, ctx->sms, ctx->stream));
+        cur ^= 1;
+    }
+    return MCEV_OK;
+}
+
+// Runs rounds of batches over the pixel queue until no pixel is undecided.
+// mode REFERENCE: every pixel to spp_max samples, statistics -> ref.
+// mode DETECT: Alg. 1 frame with the test variant in `A`.
+mcev_status run_rounds(mcev_ctx* ctx, const Frame& fr, StatsArgs A, int64_t* paths_out, int32_t* rounds_out) {
+    const int64_t npix = (int64_t)ctx->W * ctx->H;
+    const DevParams P = dev_params(ctx, false);
+    LAUNCH(launch_iota(ctx->queue[0], npix, ctx->sms, ctx->stream));
+    int64_t Q = npix, n_done = 0, paths = 0;
+    int rounds = 0, qi = 0;
+    int32_t h_count = 0;
+    while (Q > 0) {
+        const int32_t spp_r = n_done == 0 ? std::min(A.spp_min, A.spp_max)
+                                          : (int32_t)std::min<int64_t>(A.spp_batch, A.spp_max - n_done);
+        CU(cudaMemsetAsync(ctx->wave.counters + 3, 0, sizeof(int32_t), ctx->stream));
+        A.spp_r = spp_r;
+        A.k_base = n_done;
+        const int64_t per_chunk = std::max<int64_t>(1, ctx->wave.cap / spp_r);
+        for (int64_t j0 = 0; j0 < Q; j0 += per_chunk) {
+            const int64_t nj = std::min(per_chunk, Q - j0);
+            ST(trace_chunk(ctx, fr, P, ctx->queue[qi], j0, spp_r, n_done, nj * spp_r));
+            LAUNCH(launch_stats(ctx->wave, A, ctx->queue[qi], j0, nj, ctx->queue[qi ^ 1], ctx->sms, ctx->stream));
+        }
+        paths += Q * spp_r;
+        n_done += spp_r;
+        ++rounds;
+        CU(cudaMemcpyAsync(&h_count, ctx->wave.counters + 3, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+        CU(cudaStreamSynchronize(ctx->stream));
+        Q = h_count;
+        qi ^= 1;
+        if (n_done >= A.spp_max && Q != 0)
+            return fail(ctx, MCEV_ERR_STATE, "internal: %lld pixels undecided at the sample cap", (long long)Q);
+    }
+    if (paths_out) *paths_out = paths;
+    if (rounds_out) *rounds_out = rounds;
+    return MCEV_OK;
+}
+
+mcev_status check_ready(mcev_ctx* ctx) {
+    if (!ctx) return MCEV_ERR_ARG;
+    if (!ctx->have_scene) return fail(ctx, MCEV_ERR_STATE, "no scene uploaded");
+    CU(cudaSetDevice(ctx->device));
+    ST(ensure_wave(ctx));
+    ST(ensure_pixels(ctx));
+    return MCEV_OK;
+}
+
+mcev_status do_reference(mcev_ctx* ctx, double t0, int32_t spp, int64_t* paths) {
+    ST(frame_setup(ctx, t0, 0));
+    StatsArgs A{};
+    A.cur = ctx->cur;
+    A.ref = ctx->ref;
+    A.eps = ctx->params.eps;
+    A.spp_min = spp;
+    A.spp_batch = spp;
+    A.spp_max = spp;
+    A.mode = MODE_REFERENCE;
+    A.tcrit = nullptr;
+    ST(run_rounds(ctx, ctx->frames[0], A, paths, nullptr));
+    ctx->ref_valid = true;
+    ctx->ref_time = t0;
+    return MCEV_OK;
+}
+
+}  // namespace
+
+// =====================================================================================
+extern "C" {
+
+mcev_status mcev_create(mcev_ctx** out, int device, int32_t width, int32_t height) {
+    if (!out) return MCEV_ERR_ARG;
+    *out = nullptr;
+    if (width <= 0 || height <= 0 || (int64_t)width * height > (int64_t)1 << 30) return MCEV_ERR_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return MCEV_ERR_CUDA;
+    }
+    mcev_ctx* ctx = new (std::nothrow) mcev_ctx();
+    if (!ctx) return MCEV_ERR_OOM;
+    ctx->device = device;
+    ctx->W = width;
+    ctx->H = height;
+    if (cudaSetDevice(device) != cudaSuccess || cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+        cudaEventCreate(&ctx->ev0) != cudaSuccess || cudaEventCreate(&ctx->ev1) != cudaSuccess) {
+        cudaGetLastError();
+        delete ctx;
+        return MCEV_ERR_CUDA;
+    }
+    mcev_params p{};
+    p.eps = 1e-3f;
+    p.t_min = 1e-4f;
+    p.max_depth = 4;
+    p.nee = 1;
+    p.mis = 1;
+    p.spp_min = 16;
+    p.variant = MCEV_ONE_TAILED;
+    p.se_mode = MCEV_SE_PAPER;
+    p.seed = 20240815ull;
+    p.wavefront = 0;
+    ctx->params = p;
+    *out = ctx;
+    return MCEV_OK;
+}
+
+void mcev_destroy(mcev_ctx* ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    DevBuf* bufs[] = {&ctx->d_nodes, &ctx->d_tris, &ctx->d_mats, &ctx->d_env, &ctx->d_marg, &ctx->d_cond,
+                      &ctx->d_tpdf, &ctx->frames[0].buf, &ctx->frames[1].buf, &ctx->d_wave, &ctx->d_counters,
+                      &ctx->d_pix, &ctx->d_tcrit};
+    for (DevBuf* b : bufs) dev_free(ctx, *b);
+    if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+    if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+    delete ctx;
+}
+
+const char* mcev_last_error(const mcev_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+mcev_status mcev_set_stream(mcev_ctx* ctx, void* stream) {
+    if (!ctx) return MCEV_ERR_ARG;
+    ctx->stream = (cudaStream_t)stream;
+    return MCEV_OK;
+}
+
+mcev_status mcev_set_allocator(mcev_ctx* ctx, mcev_alloc_fn alloc, mcev_free_fn free_fn, void* user) {
+    if (!ctx) return MCEV_ERR_ARG;
+    if ((alloc == nullptr) != (free_fn == nullptr)) return fail(ctx, MCEV_ERR_ARG, "alloc and free must both be set");
+    if (ctx->have_scene || ctx->d_wave.ptr || ctx->d_pix.ptr)
+        return fail(ctx, MCEV_ERR_STATE, "set the allocator before uploading a scene");
+    ctx->alloc = alloc;
+    ctx->free_fn = free_fn;
+    ctx->alloc_user = user;
+    return MCEV_OK;
+}
+
+mcev_status mcev_scene_upload(mcev_ctx* ctx, const mcev_scene_desc* s) {
+    if (!ctx) return MCEV_ERR_ARG;
+    if (!s) return fail(ctx, MCEV_ERR_ARG, "null scene description");
+    if (s->n_triangles < 0 || s->n_vertices < 0 || s->n_meshes < 0 || s->n_instances < 0 || s->n_keys < 1 ||
+        s->n_materials < 1)
+        return fail(ctx, MCEV_ERR_ARG, "negative count, no keyframe or no material");
+    if (s->n_triangles > ((int64_t)1 << 30)) return fail(ctx, MCEV_ERR_ARG, "too many triangles");
+    if ((s->n_triangles > 0 && (!s->vertices || !s->triangles || !s->tri_material)) ||
+        (s->n_meshes > 0 && !s->mesh_ranges) || (s->n_instances > 0 && (!s->inst_mesh || !s->inst_material)) ||
+        !s->key_times || (s->n_instances > 0 && !s->inst_xform) || !s->cam_eye || !s->cam_target || !s->cam_up ||
+        !s->mat_type || !s->mat_albedo || !s->mat_rough || !s->mat_emit)
+        return fail(ctx, MCEV_ERR_ARG, "null array in scene description");
+    if (!(s->fov_deg > 0.0 && s->fov_deg < 180.0)) return fail(ctx, MCEV_ERR_ARG, "fov_deg out of (0, 180)");
+    for (int k = 1; k < s->n_keys; ++k)
+        if (!(s->key_times[k] > s->key_times[k - 1])) return fail(ctx, MCEV_ERR_ARG, "key times not increasing");
+    for (int64_t t = 0; t < 3 * s->n_triangles; ++t)
+        if (s->triangles[t] < 0 || s->triangles[t] >= s->n_vertices)
+            return fail(ctx, MCEV_ERR_ARG, "triangle vertex index out of range");
+    for (int64_t t = 0; t < s->n_triangles; ++t)
+        if (s->tri_material[t] < 0 || s->tri_material[t] >= s->n_materials)
+            return fail(ctx, MCEV_ERR_ARG, "triangle material out of range");
+    for (int m = 0; m < s->n_meshes; ++m) {
+        const int64_t f = s->mesh_ranges[2 * m], c = s->mesh_ranges[2 * m + 1];
+        if (f < 0 || c < 0 || f + c > s->n_triangles) return fail(ctx, MCEV_ERR_ARG, "mesh range out of bounds");
+    }
+    for (int i = 0; i < s->n_instances; ++i) {
+        if (s->inst_mesh[i] < 0 || s->inst_mesh[i] >= s->n_meshes)
+            return fail(ctx, MCEV_ERR_ARG, "instance mesh out of range");
+        if (s->inst_material[i] < -1 || s->inst_material[i] >= s->n_materials)
+            return fail(ctx, MCEV_ERR_ARG, "instance material out of range");
+    }
+    for (int m = 0; m < s->n_materials; ++m) {
+        if (s->mat_type[m] != MAT_DIFFUSE && s->mat_type[m] != MAT_GGX)
+            return fail(ctx, MCEV_ERR_ARG, "unknown material type %d", s->mat_type[m]);
+        if (s->mat_type[m] == MAT_GGX && !(s->mat_rough[m] > 0.0f))
+            return fail(ctx, MCEV_ERR_ARG, "GGX material needs rough > 0");
+        if (!(s->mat_albedo[m] >= 0.0f && s->mat_albedo[m] <= 1.0f) || !(s->mat_emit[m] >= 0.0f))
+            return fail(ctx, MCEV_ERR_ARG, "albedo outside [0,1] or negative emission");
+    }
+    if (s->env && (s->env_w <= 0 || s->env_h <= 0)) return fail(ctx, MCEV_ERR_ARG, "bad environment size");
+    if (s->env)
+        for (int64_t i = 0; i < (int64_t)s->env_w * s->env_h; ++i)
+            if (!(s->env[i] >= 0.0f) || !std::isfinite(s->env[i]))
+                return fail(ctx, MCEV_ERR_ARG, "environment texel negative or not finite");
+    CU(cudaSetDevice(ctx->device));
+    ctx->have_scene = false;
+    ctx->ref_valid = false;
+    ctx->vtx.resize(9 * (size_t)s->n_triangles);
+    ctx->tri_mat.assign(s->tri_material, s->tri_material + s->n_triangles);
+    for (int64_t t = 0; t < s->n_triangles; ++t)
+        for (int c = 0; c < 3; ++c)
+            for (int a = 0; a < 3; ++a) ctx->vtx[9 * t + 3 * c + a] = s->vertices[3 * (int64_t)s->triangles[3 * t + c] + a];
+    ctx->meshes.clear();
+    for (int m = 0; m < s->n_meshes; ++m) {
+        MeshInfo mi{};
+        mi.first_tri = s->mesh_ranges[2 * m];
+        mi.n_tri = s->mesh_ranges[2 * m + 1];
+        ctx->meshes.push_back(mi);
+    }
+    ctx->n_inst = s->n_instances;
+    ctx->inst_mesh.assign(s->inst_mesh, s->inst_mesh + s->n_instances);
+    ctx->inst_mat.assign(s->inst_material, s->inst_material + s->n_instances);
+    ctx->n_keys = s->n_keys;
+    ctx->key_t.assign(s->key_times, s->key_times + s->n_keys);
+    ctx->key_xf.assign(s->inst_xform, s->inst_xform + 12 * (size_t)s->n_keys * s->n_instances);
+    ctx->cam_eye.assign(s->cam_eye, s->cam_eye + 3 * s->n_keys);
+    ctx->cam_tgt.assign(s->cam_target, s->cam_target + 3 * s->n_keys);
+    ctx->cam_up.assign(s->cam_up, s->cam_up + 3 * s->n_keys);
+    ctx->fov_deg = s->fov_deg;
+    ctx->n_mats = s->n_materials;
+    ctx->mat_type.assign(s->mat_type, s->mat_type + s->n_materials);
+    ctx->mat_alb.assign(s->mat_albedo, s->mat_albedo + s->n_materials);
+    ctx->mat_rough.assign(s->mat_rough, s->mat_rough + s->n_materials);
+    ctx->mat_emit.assign(s->mat_emit, s->mat_emit + s->n_materials);
+    ctx->emitters.clear();
+    for (int i = 0; i < s->n_instances; ++i) {
+        const MeshInfo& m = ctx->meshes[ctx->inst_mesh[i]];
+        for (int64_t t = 0; t < m.n_tri; ++t) {
+            const int64_t prim = m.first_tri + t;
+            const int mat = ctx->inst_mat[i] >= 0 ? ctx->inst_mat[i] : ctx->tri_mat[prim];
+            if (ctx->mat_emit[mat] > 0.0f) ctx->emitters.emplace_back(i, prim);
+        }
+    }
+    std::vector<float4> mats(s->n_materials);
+    for (int m = 0; m < s->n_materials; ++m) {
+        int ty = s->mat_type[m];
+        float tf;
+        std::memcpy(&tf, &ty, 4);
+        mats[m] = make_float4(tf, s->mat_albedo[m], s->mat_rough[m], s->mat_emit[m]);
+    }
+    ST(upload(ctx, ctx->d_mats, mats.data(), mats.size() * sizeof(float4)));
+    ctx->dsc.mats = (const float4*)ctx->d_mats.ptr;
+    ctx->env_w = s->env ? s->env_w : 0;
+    ctx->env_h = s->env ? s->env_h : 0;
+    ctx->env.assign(s->env ? s->env : nullptr, s->env ? s->env + (size_t)s->env_w * s->env_h : nullptr);
+    if (s->env) {
+        ST(build_env(ctx));
+    } else {
+        ctx->env_ok = false;
+        ctx->dsc.has_env = 0;
+        ctx->dsc.env_ok = 0;
+        ctx->dsc.env_w = ctx->dsc.env_h = 0;
+    }
+    ST(build_blas(ctx));
+    ctx->have_scene = true;
+    return MCEV_OK;
+}
+
+mcev_status mcev_build_bvh(mcev_ctx* ctx, int32_t sah_bins, int32_t max_leaf) {
+    if (!ctx) return MCEV_ERR_ARG;
+    if (sah_bins < 4 || sah_bins > 256 || max_leaf < 1 || max_leaf > 16)
+        return fail(ctx, MCEV_ERR_ARG, "sah_bins in [4,256] and max_leaf in [1,16]");
+    if (!ctx->have_scene) return fail(ctx, MCEV_ERR_STATE, "no scene uploaded");
+    CU(cudaSetDevice(ctx->device));
+    ctx->sah_bins = sah_bins;
+    ctx->max_leaf = max_leaf;
+    return build_blas(ctx);
+}
+
+mcev_status mcev_set_params(mcev_ctx* ctx, const mcev_params* p) {
+    if (!ctx) return MCEV_ERR_ARG;
+    if (!p) return fail(ctx, MCEV_ERR_ARG, "null params");
+    if (!(p->eps > 0.0f) || !(p->t_min >= 0.0f) || p->max_depth < 0 || p->max_depth > 64 || p->spp_min < 2 ||
+        p->variant < 0 || p->variant > 3 || p->se_mode < 0 || p->se_mode > 1 || p->wavefront < 0 ||
+        (p->wavefront > 0 && p->wavefront < 1024) || p->wavefront > ((int64_t)1 << 30))
+        return fail(ctx, MCEV_ERR_ARG, "invalid render parameters");
+    const bool reseed = p->seed != ctx->params.seed;
+    const bool shape = p->eps != ctx->params.eps || p->t_min != ctx->params.t_min ||
+                       p->max_depth != ctx->params.max_depth || p->nee != ctx->params.nee || p->mis != ctx->params.mis;
+    ctx->params = *p;
+    if (reseed || shape) {
+        ctx->ref_valid = false;
+        for (auto& f : ctx->frames) f.valid = false;
+    }
+    return MCEV_OK;
+}
+
+mcev_status mcev_render_reference(mcev_ctx* ctx, double t0, int32_t spp) {
+    ST(check_ready(ctx));
+    if (spp < 2) return fail(ctx, MCEV_ERR_ARG, "spp must be >= 2");
+    ctx->launches = 0;
+    return do_reference(ctx, t0, spp, nullptr);
+}
+
+mcev_status mcev_render_events(mcev_ctx* ctx, double t0, double t1, float C, float alpha, int32_t spp_batch,
+                               int32_t spp_max, int8_t* events_out, int32_t* spp_out, float* mean_out,
+                               mcev_stats* stats_out) {
+    ST(check_ready(ctx));
+    if (!events_out) return fail(ctx, MCEV_ERR_ARG, "events_out is required");
+    if (!(C >= 0.0f) || !(alpha > 0.0f && alpha < 1.0f) || spp_batch < 1 || spp_max < ctx->params.spp_min)
+        return fail(ctx, MCEV_ERR_ARG, "need C >= 0, 0 < alpha < 1, spp_batch >= 1, spp_max >= spp_min");
+    ctx->launches = 0;
+    CU(cudaEventRecord(ctx->ev0, ctx->stream));
+    int64_t ref_paths = 0, paths = 0;
+    int32_t rounds = 0;
+    if (!ctx->ref_valid || ctx->ref_time != t0) ST(do_reference(ctx, t0, spp_max, &ref_paths));
+    ST(frame_setup(ctx, t1, 1));
+    ST(ensure_tcrit(ctx, alpha, ctx->params.variant, ctx->params.spp_min, spp_batch, spp_max));
+    CU(cudaMemsetAsync(ctx->wave.counters + 4, 0, 12 * sizeof(int32_t), ctx->stream));
+    StatsArgs A{};
+    A.cur = ctx->cur;
+    A.ref = ctx->ref;
+    A.tcrit = (const float*)ctx->d_tcrit.ptr;
+    A.events = events_out;
+    A.spp_out = spp_out;
+    A.mean_out = mean_out;
+    A.eps = ctx->params.eps;
+    A.C = C;
+    A.spp_min = ctx->params.spp_min;
+    A.spp_batch = spp_batch;
+    A.spp_max = spp_max;
+    A.mode = MODE_DETECT;
+    A.variant = ctx->params.variant;
+    A.se_mode = ctx->params.se_mode;
+    ST(run_rounds(ctx, ctx->frames[1], A, &paths, &rounds));
+    ctx->ref_valid = true;
+    ctx->ref_time = t1;
+    CU(cudaEventRecord(ctx->ev1, ctx->stream));
+    if (stats_out) {
+        int32_t c[16];
+        CU(cudaMemcpyAsync(c, ctx->wave.counters, sizeof c, cudaMemcpyDeviceToHost, ctx->stream));
+        CU(cudaStreamSynchronize(ctx->stream));
+        float ms = 0.0f;
+        CU(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
+        std::memset(stats_out, 0, sizeof *stats_out);
+        stats_out->paths = paths;
+        stats_out->ref_paths = ref_paths;
+        stats_out->rounds = rounds;
+        stats_out->kernel_launches = ctx->launches;
+        stats_out->nonfinite = c[4];
+        stats_out->events_pos = c[5];
+        stats_out->events_neg = c[6];
+        stats_out->pixels_at_cap = c[7];
+        stats_out->gpu_ms = ms;
+        if (c[15]) return fail(ctx, MCEV_ERR_STATE, "traversal stack overflow");
+    }
+    return MCEV_OK;
+}
+
+mcev_status mcev_trace_samples(mcev_ctx* ctx, double t, const int32_t* pixels, int64_t n_pix, int64_t k0,
+                               int32_t count, float* L_out, uint32_t* sig_out) {
+    ST(check_ready(ctx));
+    if (!pixels || !L_out || n_pix < 0 || k0 < 0 || count < 1 || k0 + count > ((int64_t)1 << 32))
+        return fail(ctx, MCEV_ERR_ARG, "bad trace_samples arguments");
+    if (n_pix == 0) return MCEV_OK;
+    ctx->launches = 0;
+    ST(frame_setup(ctx, t, 0));
+    const DevParams P = dev_params(ctx, sig_out != nullptr);
+    const int64_t per_chunk = std::max<int64_t>(1, ctx->wave.cap / count);
+    for (int64_t j0 = 0; j0 < n_pix; j0 += per_chunk) {
+        const int64_t nj = std::min(per_chunk, n_pix - j0);
+        ST(trace_chunk(ctx, ctx->frames[0], P, pixels, j0, count, k0, nj * count));
+        LAUNCH(launch_write_samples(ctx->wave, j0 * count, nj * count, L_out, sig_out, ctx->sms, ctx->stream));
+    }
+    return MCEV_OK;
+}
+
+size_t mcev_state_bytes(const mcev_ctx* ctx) {
+    if (!ctx) return 0;
+    return 16 + 12 * (size_t)ctx->W * ctx->H;
+}
+
+mcev_status mcev_get_state(mcev_ctx* ctx, void* dev_buf, size_t bytes) {
+    if (!ctx) return MCEV_ERR_ARG;
+    if (!dev_buf || bytes != mcev_state_bytes(ctx)) return fail(ctx, MCEV_ERR_ARG, "state buffer size mismatch");
+    CU(cudaSetDevice(ctx->device));
+    ST(ensure_pixels(ctx));
+    const size_t n = (size_t)ctx->W * ctx->H;
+    char hdr[16] = {0};
+    int32_t valid = ctx->ref_valid ? 1 : 0, npx = (int32_t)n;
+    std::memcpy(hdr, &ctx->ref_time, 8);
+    std::memcpy(hdr + 8, &valid, 4);
+    std::memcpy(hdr + 12, &npx, 4);
+    char* d = (char*)dev_buf;
+    CU(cudaMemcpyAsync(d, hdr, 16, cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(d + 16, ctx->ref.n, 4 * n, cudaMemcpyDeviceToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(d + 16 + 4 * n, ctx->ref.mean, 4 * n, cudaMemcpyDeviceToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(d + 16 + 8 * n, ctx->ref.m2, 4 * n, cudaMemcpyDeviceToDevice, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    return MCEV_OK;
+}
+
+mcev_status mcev_set_state(mcev_ctx* ctx, const void* dev_buf, size_t bytes) {
+    if (!ctx) return MCEV_ERR_ARG;
+    if (!dev_buf || bytes != mcev_state_bytes(ctx)) return fail(ctx, MCEV_ERR_ARG, "state buffer size mismatch");
+    CU(cudaSetDevice(ctx->device));
+    ST(ensure_pixels(ctx));
+    const size_t n = (size_t)ctx->W * ctx->H;
+    char hdr[16];
+    const char* s = (const char*)dev_buf;
+    CU(cudaMemcpyAsync(hdr, s, 16, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaMemcpyAsync(ctx->ref.n, s + 16, 4 * n, cudaMemcpyDeviceToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(ctx->ref.mean, s + 16 + 4 * n, 4 * n, cudaMemcpyDeviceToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(ctx->ref.m2, s + 16 + 8 * n, 4 * n, cudaMemcpyDeviceToDevice, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    int32_t valid, npx;
+    std::memcpy(&ctx->ref_time, hdr, 8);
+    std::memcpy(&valid, hdr + 8, 4);
+    std::memcpy(&npx, hdr + 12, 4);
+    if (npx != (int32_t)n) {
+        ctx->ref_valid = false;
+        return fail(ctx, MCEV_ERR_ARG, "state blob is for %d pixels, context has %zu", npx, n);
+    }
+    ctx->ref_valid = valid != 0;
+    return MCEV_OK;
+}
+
+}  // extern "C"

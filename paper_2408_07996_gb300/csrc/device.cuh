@@ -1,0 +1,505 @@
+// device.cuh -- device-side building blocks of the path tracer (FP32).
+//
+// Scene and sampling conventions (they define the samples the method
+// averages, Sec. 3.1, and are restated independently by the test oracle):
+//  * Philox4x32-10 (Salmon et al., SC 2011); counter (pixel, sample, vertex,
+//    block), key (seed_lo ^ frame key, seed_hi); u = (x >> 8) * 2^-24.
+//  * pinhole camera, box-filtered jitter, field of view on the shorter axis;
+//  * watertight ray/triangle test (Woop, Benthin, Wald, JCGT 2013);
+//  * Lambertian (cosine sampling) and GGX with Smith height-correlated
+//    masking, Schlick Fresnel and visible-normal sampling (Heitz, JCGT 2018);
+//  * lat-long environment, piecewise-constant importance sampling;
+//  * uniform choice among emissive triangles, uniform area sampling.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "layout.h"
+
+namespace mcev {
+
+#define MCEV_PI 3.14159265358979323846f
+#define MCEV_STACK MCEV_STACK_HOST
+
+// ------------------------------------------------------------------ math
+struct f3 {
+    float x, y, z;
+};
+__device__ __forceinline__ f3 mk3(float x, float y, float z) { return f3{x, y, z}; }
+__device__ __forceinline__ f3 operator+(f3 a, f3 b) { return mk3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ f3 operator-(f3 a, f3 b) { return mk3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ f3 operator*(f3 a, float s) { return mk3(a.x * s, a.y * s, a.z * s); }
+__device__ __forceinline__ float dot3(f3 a, f3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ f3 cross3(f3 a, f3 b) {
+    return mk3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ f3 norm3(f3 a) { return a * (1.0f / sqrtf(dot3(a, a))); }
+__device__ __forceinline__ f3 xyz(float4 v) { return mk3(v.x, v.y, v.z); }
+
+// row-major 3x4 affine (rows r0, r1, r2)
+__device__ __forceinline__ f3 xf_point(float4 r0, float4 r1, float4 r2, f3 p) {
+    return mk3(r0.x * p.x + r0.y * p.y + r0.z * p.z + r0.w, r1.x * p.x + r1.y * p.y + r1.z * p.z + r1.w,
+               r2.x * p.x + r2.y * p.y + r2.z * p.z + r2.w);
+}
+__device__ __forceinline__ f3 xf_vec(float4 r0, float4 r1, float4 r2, f3 p) {
+    return mk3(r0.x * p.x + r0.y * p.y + r0.z * p.z, r1.x * p.x + r1.y * p.y + r1.z * p.z,
+               r2.x * p.x + r2.y * p.y + r2.z * p.z);
+}
+// (A^-1)^T n from the rows of the inverse
+__device__ __forceinline__ f3 xf_normal(float4 i0, float4 i1, float4 i2, f3 n) {
+    return mk3(i0.x * n.x + i1.x * n.y + i2.x * n.z, i0.y * n.x + i1.y * n.y + i2.y * n.z,
+               i0.z * n.x + i1.z * n.y + i2.z * n.z);
+}
+
+// ------------------------------------------------------------------ Philox4x32-10
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    }
+    return c;
+}
+__device__ __forceinline__ float u01(uint32_t x) { return (float)(x >> 8) * 0x1p-24f; }
+
+// ------------------------------------------------------------------ ONB (Duff et al. 2017)
+__device__ __forceinline__ void onb(f3 n, f3& t, f3& b) {
+    const float sg = n.z >= 0.0f ? 1.0f : -1.0f;
+    const float a = -1.0f / (sg + n.z);
+    const float bb = n.x * n.y * a;
+    t = mk3(1.0f + sg * n.x * n.x * a, sg * bb, -sg * n.x);
+    b = mk3(bb, sg + n.y * n.y * a, -n.y);
+}
+
+// ------------------------------------------------------------------ BSDFs (local frame, n = +z)
+__device__ __forceinline__ float ggx_lambda(float a, float z) {
+    const float t2 = (1.0f - z * z) / (z * z);
+    return 0.5f * (-1.0f + sqrtf(1.0f + a * a * t2));
+}
+
+// returns f(wo, wi); *pdf = pdf of sampling wi
+__device__ __forceinline__ float bsdf_eval(int type, float albedo, float rough, f3 wo, f3 wi, float* pdf) {
+    *pdf = 0.0f;
+    if (!(wo.z > 0.0f) || !(wi.z > 0.0f)) return 0.0f;
+    if (type == MAT_DIFFUSE) {
+        *pdf = wi.z * (1.0f / MCEV_PI);
+        return albedo * (1.0f / MCEV_PI);
+    }
+    const f3 h = norm3(wo + wi);
+    const float a2 = rough * rough;
+    const float k = h.z * h.z * (a2 - 1.0f) + 1.0f;
+    const float D = a2 / (MCEV_PI * k * k);
+    const float lo = ggx_lambda(rough, wo.z), li = ggx_lambda(rough, wi.z);
+    const float G1 = 1.0f / (1.0f + lo);
+    const float G2 = 1.0f / (1.0f + lo + li);
+    const float c = dot3(wi, h);
+    const float m = 1.0f - c;
+    const float m2 = m * m;
+    const float F = albedo + (1.0f - albedo) * (m2 * m2 * m);
+    *pdf = G1 * D / (4.0f * wo.z);
+    return F * D * G2 / (4.0f * wo.z * wi.z);
+}
+
+__device__ __forceinline__ f3 bsdf_sample(int type, float rough, f3 wo, float u1, float u2) {
+    float s, c;
+    sincosf(2.0f * MCEV_PI * u2, &s, &c);
+    if (type == MAT_DIFFUSE) {
+        const float r = sqrtf(u1);
+        return mk3(r * c, r * s, sqrtf(fmaxf(0.0f, 1.0f - u1)));
+    }
+    const float a = rough;
+    const f3 Vh = norm3(mk3(a * wo.x, a * wo.y, wo.z));
+    const float lensq = Vh.x * Vh.x + Vh.y * Vh.y;
+    const f3 T1 = lensq > 0.0f ? mk3(-Vh.y, Vh.x, 0.0f) * (1.0f / sqrtf(lensq)) : mk3(1.0f, 0.0f, 0.0f);
+    const f3 T2 = cross3(Vh, T1);
+    const float r = sqrtf(u1);
+    const float t1 = r * c;
+    float t2 = r * s;
+    const float sh = 0.5f * (1.0f + Vh.z);
+    t2 = (1.0f - sh) * sqrtf(1.0f - t1 * t1) + sh * t2;
+    const f3 Nh = T1 * t1 + T2 * t2 + Vh * sqrtf(fmaxf(0.0f, 1.0f - t1 * t1 - t2 * t2));
+    const f3 Ne = norm3(mk3(a * Nh.x, a * Nh.y, fmaxf(0.0f, Nh.z)));
+    const float d = dot3(wo, Ne);
+    return Ne * (2.0f * d) - wo;
+}
+
+// ------------------------------------------------------------------ environment
+__device__ __forceinline__ void env_texel(const DevScene& sc, f3 d, int& row, int& col, float& sin_t) {
+    const float cy = fminf(1.0f, fmaxf(-1.0f, d.y));
+    const float theta = acosf(cy);
+    float phi = atan2f(d.z, d.x);
+    if (phi < 0.0f) phi += 2.0f * MCEV_PI;
+    col = min((int)(phi / (2.0f * MCEV_PI) * (float)sc.env_w), sc.env_w - 1);
+    row = min((int)(theta / MCEV_PI * (float)sc.env_h), sc.env_h - 1);
+    sin_t = sinf(theta);
+}
+
+__device__ __forceinline__ float texel_pdf(const DevScene& sc, int row, int col, float sin_t) {
+    if (!sc.env_ok || !(sin_t > 0.0f)) return 0.0f;
+    return __ldg(sc.env_tpdf + (int64_t)row * sc.env_w + col) / sin_t;
+}
+
+// smallest k in [0, n) with u < cdf[k + 1]
+__device__ __forceinline__ int cdf_pick(const float* cdf, int n, float u) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (u < __ldg(cdf + mid + 1)) hi = mid;
+        else lo = mid + 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ f3 env_sample(const DevScene& sc, float u1, float u2, float& pdf, float& Le) {
+    const int row = cdf_pick(sc.env_marg, sc.env_h, u1);
+    const float m0 = __ldg(sc.env_marg + row), m1 = __ldg(sc.env_marg + row + 1);
+    const float dv = (u1 - m0) / (m1 - m0);
+    const float* c = sc.env_cond + (int64_t)row * (sc.env_w + 1);
+    const int col = cdf_pick(c, sc.env_w, u2);
+    const float c0 = __ldg(c + col), c1 = __ldg(c + col + 1);
+    const float du = (u2 - c0) / (c1 - c0);
+    const float theta = MCEV_PI * ((float)row + dv) / (float)sc.env_h;
+    const float phi = 2.0f * MCEV_PI * ((float)col + du) / (float)sc.env_w;
+    float st, ct, sp, cp;
+    sincosf(theta, &st, &ct);
+    sincosf(phi, &sp, &cp);
+    Le = __ldg(sc.env + (int64_t)row * sc.env_w + col);
+    pdf = texel_pdf(sc, row, col, st);
+    return mk3(st * cp, ct, st * sp);
+}
+
+__device__ __forceinline__ float power_heuristic(float a, float b) {
+    const float a2 = a * a, b2 = b * b;
+    return a2 / (a2 + b2);
+}
+
+__device__ __forceinline__ uint32_t fnv(uint32_t h, uint32_t w) { return (h ^ w) * 16777619u; }
+
+// ------------------------------------------------------------------ intersection
+// Watertight test: the ray is sheared so it becomes the +z axis; 2D edge
+// functions U, V, W of the sheared vertices decide containment.
+struct WRay {
+    f3 o;
+    f3 mx, my, mz;    // shear rows: x' = mx.A, y' = my.A, z' = mz.A for A = v - o
+    f3 idir;          // 1/d with tiny components replaced, for slab tests
+    f3 oidir;         // o * idir
+};
+
+__device__ __forceinline__ WRay make_wray(f3 o, f3 d) {
+    WRay r;
+    r.o = o;
+    const float ax = fabsf(d.x), ay = fabsf(d.y), az = fabsf(d.z);
+    int kz = 0;
+    if (ay > ax && ay >= az) kz = 1;
+    else if (az > ax && az > ay) kz = 2;
+    int kx = kz == 2 ? 0 : kz + 1;
+    int ky = kx == 2 ? 0 : kx + 1;
+    const float dz = kz == 0 ? d.x : (kz == 1 ? d.y : d.z);
+    if (dz < 0.0f) {
+        const int t = kx;
+        kx = ky;
+        ky = t;
+    }
+    const float dkx = kx == 0 ? d.x : (kx == 1 ? d.y : d.z);
+    const float dky = ky == 0 ? d.x : (ky == 1 ? d.y : d.z);
+    const float Sx = dkx / dz, Sy = dky / dz, Sz = 1.0f / dz;
+    r.mx = mk3(kx == 0 ? 1.0f : 0.0f, kx == 1 ? 1.0f : 0.0f, kx == 2 ? 1.0f : 0.0f);
+    r.my = mk3(ky == 0 ? 1.0f : 0.0f, ky == 1 ? 1.0f : 0.0f, ky == 2 ? 1.0f : 0.0f);
+    r.mz = mk3(kz == 0 ? Sz : 0.0f, kz == 1 ? Sz : 0.0f, kz == 2 ? Sz : 0.0f);
+    if (kz == 0) { r.mx.x = -Sx; r.my.x = -Sy; }
+    if (kz == 1) { r.mx.y = -Sx; r.my.y = -Sy; }
+    if (kz == 2) { r.mx.z = -Sx; r.my.z = -Sy; }
+    const float ooeps = 0x1p-80f;
+    r.idir = mk3(1.0f / (fabsf(d.x) > ooeps ? d.x : copysignf(ooeps, d.x)),
+                 1.0f / (fabsf(d.y) > ooeps ? d.y : copysignf(ooeps, d.y)),
+                 1.0f / (fabsf(d.z) > ooeps ? d.z : copysignf(ooeps, d.z)));
+    r.oidir = mk3(o.x * r.idir.x, o.y * r.idir.y, o.z * r.idir.z);
+    return r;
+}
+
+// returns t in (tmin, tmax) or -1 (no hit); tmax inclusive when `incl`
+__device__ __forceinline__ float tri_hit(const WRay& r, float4 p0, float4 p1, float4 p2, float tmin, float tmax) {
+    const f3 A = xyz(p0) - r.o, B = xyz(p1) - r.o, C = xyz(p2) - r.o;
+    const float Ax = dot3(r.mx, A), Ay = dot3(r.my, A);
+    const float Bx = dot3(r.mx, B), By = dot3(r.my, B);
+    const float Cx = dot3(r.mx, C), Cy = dot3(r.my, C);
+    const float U = Cx * By - Cy * Bx;
+    const float V = Ax * Cy - Ay * Cx;
+    const float W = Bx * Ay - By * Ax;
+    if ((U < 0.0f || V < 0.0f || W < 0.0f) && (U > 0.0f || V > 0.0f || W > 0.0f)) return -1.0f;
+    const float det = U + V + W;
+    if (det == 0.0f) return -1.0f;
+    const float T = U * dot3(r.mz, A) + V * dot3(r.mz, B) + W * dot3(r.mz, C);
+    const float t = T / det;
+    return (t > tmin && t <= tmax) ? t : -1.0f;
+}
+
+// slab test of both children of a node; returns hit mask (bit0 left, bit1 right)
+__device__ __forceinline__ int node_hits(const WRay& r, const Node& n, float tmin, float tmax, float& tl, float& tr) {
+    const float4 a = n.a, b = n.b, c = n.c;
+    const float lx0 = a.x * r.idir.x - r.oidir.x, lx1 = a.y * r.idir.x - r.oidir.x;
+    const float ly0 = a.z * r.idir.y - r.oidir.y, ly1 = a.w * r.idir.y - r.oidir.y;
+    const float lz0 = c.x * r.idir.z - r.oidir.z, lz1 = c.y * r.idir.z - r.oidir.z;
+    const float rx0 = b.x * r.idir.x - r.oidir.x, rx1 = b.y * r.idir.x - r.oidir.x;
+    const float ry0 = b.z * r.idir.y - r.oidir.y, ry1 = b.w * r.idir.y - r.oidir.y;
+    const float rz0 = c.z * r.idir.z - r.oidir.z, rz1 = c.w * r.idir.z - r.oidir.z;
+    const float ln = fmaxf(fmaxf(fminf(lx0, lx1), fminf(ly0, ly1)), fmaxf(fminf(lz0, lz1), tmin));
+    const float lf = fminf(fminf(fmaxf(lx0, lx1), fmaxf(ly0, ly1)), fminf(fmaxf(lz0, lz1), tmax));
+    const float rn = fmaxf(fmaxf(fminf(rx0, rx1), fminf(ry0, ry1)), fmaxf(fminf(rz0, rz1), tmin));
+    const float rf = fminf(fminf(fmaxf(rx0, rx1), fmaxf(ry0, ry1)), fminf(fmaxf(rz0, rz1), tmax));
+    tl = ln;
+    tr = rn;
+    // (1 + 2^-20) slack keeps rounding in the slab arithmetic from culling a hit
+    return (ln <= lf * 1.000001f + 1e-30f ? 1 : 0) | (rn <= rf * 1.000001f + 1e-30f ? 2 : 0);
+}
+
+__device__ __forceinline__ Node load_node(const Node* nodes, int i) {
+    const float4* p = reinterpret_cast<const float4*>(nodes + i);
+    Node n;
+    n.a = __ldg(p);
+    n.b = __ldg(p + 1);
+    n.c = __ldg(p + 2);
+    const float4 d = __ldg(p + 3);
+    n.d = make_int4(__float_as_int(d.x), __float_as_int(d.y), __float_as_int(d.z), __float_as_int(d.w));
+    return n;
+}
+
+struct Hit {
+    float t;
+    int inst;
+    int tri;    // leaf-order triangle index
+    int prim;   // uploaded triangle id (ties)
+};
+
+__device__ __forceinline__ bool better_hit(float t, int inst, int prim, const Hit& h) {
+    if (t < h.t) return true;
+    if (t > h.t) return false;
+    if (inst != h.inst) return inst < h.inst;
+    return prim < h.prim;
+}
+
+// BLAS closest hit of an object-space ray; updates h
+__device__ __forceinline__ void blas_closest(const DevScene& sc, int root, int inst, const WRay& r,
+                                             float tmin, Hit& h, int* stack, int base, int* err) {
+    int sp = base;
+    int node = root;
+    while (true) {
+        const Node n = load_node(sc.nodes, node);
+        float tl, tr;
+        const int m = node_hits(r, n, tmin, h.t, tl, tr);
+        int next = -0x7fffffff;
+        // leaves: test triangles immediately
+        if ((m & 1) && n.d.x < 0) {
+            const int first = ~n.d.x;
+            for (int i = 0; i < n.d.z; ++i) {
+                const float4* tp = sc.tris + 3 * (first + i);
+                const float4 p0 = __ldg(tp), p1 = __ldg(tp + 1), p2 = __ldg(tp + 2);
+                const float t = tri_hit(r, p0, p1, p2, tmin, h.t);
+                if (t >= 0.0f && better_hit(t, inst, __float_as_int(p0.w), h)) {
+                    h.t = t; h.inst = inst; h.tri = first + i; h.prim = __float_as_int(p0.w);
+                }
+            }
+        }
+        if ((m & 2) && n.d.y < 0) {
+            const int first = ~n.d.y;
+            for (int i = 0; i < n.d.w; ++i) {
+                const float4* tp = sc.tris + 3 * (first + i);
+                const float4 p0 = __ldg(tp), p1 = __ldg(tp + 1), p2 = __ldg(tp + 2);
+                const float t = tri_hit(r, p0, p1, p2, tmin, h.t);
+                if (t >= 0.0f && better_hit(t, inst, __float_as_int(p0.w), h)) {
+                    h.t = t; h.inst = inst; h.tri = first + i; h.prim = __float_as_int(p0.w);
+                }
+            }
+        }
+        const bool gl = (m & 1) && n.d.x >= 0 && tl <= h.t;
+        const bool gr = (m & 2) && n.d.y >= 0 && tr <= h.t;
+        if (gl && gr) {
+            const int nearc = tl <= tr ? n.d.x : n.d.y;
+            const int farc = tl <= tr ? n.d.y : n.d.x;
+            if (sp < MCEV_STACK) stack[sp++] = farc;
+            else *err = 1;
+            next = nearc;
+        } else if (gl) {
+            next = n.d.x;
+        } else if (gr) {
+            next = n.d.y;
+        }
+        if (next == -0x7fffffff) {
+            if (sp == base) break;
+            next = stack[--sp];
+        }
+        node = next;
+    }
+}
+
+__device__ __forceinline__ bool blas_any(const DevScene& sc, int root, const WRay& r, float tmin, float tmax,
+                                         int* stack, int base, int* err) {
+    int sp = base;
+    int node = root;
+    while (true) {
+        const Node n = load_node(sc.nodes, node);
+        float tl, tr;
+        const int m = node_hits(r, n, tmin, tmax, tl, tr);
+        for (int side = 0; side < 2; ++side) {
+            const int child = side ? n.d.y : n.d.x;
+            const int cnt = side ? n.d.w : n.d.z;
+            if ((m & (1 << side)) && child < 0) {
+                const int first = ~child;
+                for (int i = 0; i < cnt; ++i) {
+                    const float4* tp = sc.tris + 3 * (first + i);
+                    if (tri_hit(r, __ldg(tp), __ldg(tp + 1), __ldg(tp + 2), tmin, tmax) >= 0.0f) return true;
+                }
+            }
+        }
+        const bool gl = (m & 1) && n.d.x >= 0;
+        const bool gr = (m & 2) && n.d.y >= 0;
+        int next = -0x7fffffff;
+        if (gl && gr) {
+            if (sp < MCEV_STACK) stack[sp++] = n.d.y;
+            else *err = 1;
+            next = n.d.x;
+        } else if (gl) {
+            next = n.d.x;
+        } else if (gr) {
+            next = n.d.y;
+        }
+        if (next == -0x7fffffff) {
+            if (sp == base) return false;
+            next = stack[--sp];
+        }
+        node = next;
+    }
+}
+
+// instance record: rows M0..M2, Minv0..Minv2, (root, override, 0, 0)
+__device__ __forceinline__ WRay object_ray(const DevFrame& fr, int inst, f3 o, f3 d, int& root) {
+    const float4* ip = fr.inst + 7 * inst;
+    const float4 i0 = __ldg(ip + 3), i1 = __ldg(ip + 4), i2 = __ldg(ip + 5);
+    root = __float_as_int(__ldg(ip + 6).x);
+    return make_wray(xf_point(i0, i1, i2, o), xf_vec(i0, i1, i2, d));
+}
+
+// world-space closest hit over the two-level hierarchy
+__device__ __forceinline__ Hit closest_hit(const DevScene& sc, const DevFrame& fr, f3 o, f3 d, float tmin, int* err) {
+    Hit h;
+    h.t = __int_as_float(0x7f800000);
+    h.inst = -1;
+    h.tri = -1;
+    h.prim = -1;
+    int stack[MCEV_STACK];
+    if (fr.n_inst == 0) return h;
+    if (fr.tlas_is_leaf) {
+        int root;
+        const WRay r = object_ray(fr, 0, o, d, root);
+        blas_closest(sc, root, 0, r, tmin, h, stack, 0, err);
+        return h;
+    }
+    const WRay wr = make_wray(o, d);
+    int sp = 0;
+    int node = 0;
+    while (true) {
+        const Node n = load_node(fr.tlas, node);
+        float tl, tr;
+        const int m = node_hits(wr, n, tmin, h.t, tl, tr);
+        for (int side = 0; side < 2; ++side) {
+            const int child = side ? n.d.y : n.d.x;
+            const int cnt = side ? n.d.w : n.d.z;
+            if ((m & (1 << side)) && child < 0) {
+                for (int i = 0; i < cnt; ++i) {
+                    const int inst = ~child + i;
+                    int root;
+                    const WRay r = object_ray(fr, inst, o, d, root);
+                    blas_closest(sc, root, inst, r, tmin, h, stack, sp, err);
+                }
+            }
+        }
+        const bool gl = (m & 1) && n.d.x >= 0 && tl <= h.t;
+        const bool gr = (m & 2) && n.d.y >= 0 && tr <= h.t;
+        int next = -0x7fffffff;
+        if (gl && gr) {
+            const int nearc = tl <= tr ? n.d.x : n.d.y;
+            const int farc = tl <= tr ? n.d.y : n.d.x;
+            if (sp < MCEV_STACK) stack[sp++] = farc;
+            else *err = 1;
+            next = nearc;
+        } else if (gl) {
+            next = n.d.x;
+        } else if (gr) {
+            next = n.d.y;
+        }
+        if (next == -0x7fffffff) {
+            if (sp == 0) break;
+            next = stack[--sp];
+        }
+        node = next;
+    }
+    return h;
+}
+
+__device__ __forceinline__ bool occluded(const DevScene& sc, const DevFrame& fr, f3 o, f3 d, float tmin, float tmax,
+                                         int* err) {
+    int stack[MCEV_STACK];
+    if (fr.n_inst == 0) return false;
+    if (fr.tlas_is_leaf) {
+        int root;
+        const WRay r = object_ray(fr, 0, o, d, root);
+        return blas_any(sc, root, r, tmin, tmax, stack, 0, err);
+    }
+    const WRay wr = make_wray(o, d);
+    int sp = 0;
+    int node = 0;
+    while (true) {
+        const Node n = load_node(fr.tlas, node);
+        float tl, tr;
+        const int m = node_hits(wr, n, tmin, tmax, tl, tr);
+        for (int side = 0; side < 2; ++side) {
+            const int child = side ? n.d.y : n.d.x;
+            const int cnt = side ? n.d.w : n.d.z;
+            if ((m & (1 << side)) && child < 0) {
+                for (int i = 0; i < cnt; ++i) {
+                    const int inst = ~child + i;
+                    int root;
+                    const WRay r = object_ray(fr, inst, o, d, root);
+                    if (blas_any(sc, root, r, tmin, tmax, stack, sp, err)) return true;
+                }
+            }
+        }
+        const bool gl = (m & 1) && n.d.x >= 0;
+        const bool gr = (m & 2) && n.d.y >= 0;
+        int next = -0x7fffffff;
+        if (gl && gr) {
+            if (sp < MCEV_STACK) stack[sp++] = n.d.y;
+            else *err = 1;
+            next = n.d.x;
+        } else if (gl) {
+            next = n.d.x;
+        } else if (gr) {
+            next = n.d.y;
+        }
+        if (next == -0x7fffffff) {
+            if (sp == 0) return false;
+            next = stack[--sp];
+        }
+        node = next;
+    }
+}
+
+// ------------------------------------------------------------------ warp-aggregated append
+__device__ __forceinline__ int warp_append(int* counter, bool pred) {
+    const unsigned mask = __activemask();
+    const unsigned ballot = __ballot_sync(mask, pred);
+    if (!pred) return -1;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(ballot) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(counter, __popc(ballot));
+    base = __shfl_sync(ballot, base, leader);
+    return base + __popc(ballot & ((1u << lane) - 1u));
+}
+
+}  // namespace mcev

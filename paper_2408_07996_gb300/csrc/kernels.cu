@@ -1,0 +1,429 @@
+// kernels.cu -- wavefront path tracer and statistical event detector.
+//
+// One chunk of paths goes through
+//   raygen -> [extend -> shade(+NEE) -> shadow] x (max_depth + 1) -> stats
+// where extend/shade/shadow consume device-side ray queues (sizes in device
+// counters, no host round trip) and `stats` fuses, per queued pixel, the
+// log-luminance batch statistics (Sec. 3.1, Eq. 2-3), the Chan merge into the
+// running statistics, the t-test of Eq. 5 (Sec. 3.2), the warp-aggregated
+// re-queue of undecided pixels (Sec. 3.3) and the event rule with the
+// reference update (Alg. 1, Eq. 1).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "device.cuh"
+#include "kernels.h"
+
+namespace mcev {
+
+static constexpr uint32_t NO_FLAGS = 0xFFFFFFFFu;
+static constexpr uint32_t FNV_BASIS = 2166136261u;
+
+// ------------------------------------------------------------------ raygen
+__global__ void __launch_bounds__(256) k_raygen(DevFrame fr, DevParams P, Wave w, const int32_t* __restrict__ queue,
+                                                int64_t j0, int32_t spp_r, int64_t k_base, int64_t n_paths, int cur) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        w.counters[cur] = (int32_t)n_paths;
+        w.counters[1 - cur] = 0;
+        w.counters[2] = 0;
+    }
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n_paths; p += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = p / spp_r;
+        const int32_t s = (int32_t)(p - j * spp_r);
+        const int32_t pix = __ldg(queue + j0 + j);
+        const uint32_t k = (uint32_t)(k_base + s);
+        const uint4 x = philox4x32_10(make_uint4((uint32_t)pix, k, 0u, 0u), fr.key0, fr.key1);
+        const int px = pix % P.width, py = pix / P.width;
+        const float fx = 2.0f * ((float)px + u01(x.x)) / (float)P.width - 1.0f;
+        const float fy = 1.0f - 2.0f * ((float)py + u01(x.y)) / (float)P.height;
+        const f3 d = norm3(mk3(fr.fwd[0] + fx * fr.right[0] + fy * fr.up[0],
+                               fr.fwd[1] + fx * fr.right[1] + fy * fr.up[1],
+                               fr.fwd[2] + fx * fr.right[2] + fy * fr.up[2]));
+        w.ray_o[cur][p] = make_float4(fr.eye[0], fr.eye[1], fr.eye[2], __int_as_float((int)p));
+        w.ray_d[cur][p] = make_float4(d.x, d.y, d.z, __int_as_float(0));
+        w.beta[p] = 1.0f;
+        w.L[p] = 0.0f;
+        w.pdf_prev[p] = 0.0f;
+        w.pix_k[p] = make_int2(pix, (int)k);
+        if (P.want_sig) {
+            w.sig[p] = FNV_BASIS;
+            w.pflags[p] = NO_FLAGS;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ extend
+__global__ void __launch_bounds__(128) k_extend(DevScene sc, DevFrame fr, float t_min, Wave w, int cur, int32_t* err) {
+    const int32_t n = *(volatile int32_t*)(w.counters + cur);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        w.counters[1 - cur] = 0;
+        w.counters[2] = 0;
+    }
+    int e = 0;
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float4 o = w.ray_o[cur][i];
+        const float4 d = w.ray_d[cur][i];
+        const Hit h = closest_hit(sc, fr, xyz(o), xyz(d), t_min, &e);
+        w.hit[i] = make_float4(h.t, __int_as_float(h.inst), __int_as_float(h.tri), 0.0f);
+    }
+    if (e) atomicOr(err, 1);
+}
+
+// ------------------------------------------------------------------ shade + NEE + BSDF sampling
+__global__ void __launch_bounds__(128) k_shade(DevScene sc, DevFrame fr, DevParams P, Wave w, int cur) {
+    const int32_t n = *(volatile int32_t*)(w.counters + cur);
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float4 ro = w.ray_o[cur][i];
+        const float4 rd = w.ray_d[cur][i];
+        const int p = __float_as_int(ro.w);
+        const int depth = __float_as_int(rd.w);
+        const float4 hv = w.hit[i];
+        const int inst = __float_as_int(hv.y);
+        float beta = w.beta[p];
+        float L = w.L[p];
+        const float pdf_prev = w.pdf_prev[p];
+        uint32_t sig = 0, pflags = NO_FLAGS;
+        if (P.want_sig) {
+            sig = w.sig[p];
+            const uint32_t pf = w.pflags[p];
+            if (pf != NO_FLAGS) sig = fnv(sig, pf);
+        }
+        const f3 d = xyz(rd);
+        bool cont = false, shadow = false;
+        f3 P0 = mk3(0, 0, 0), wi_next = mk3(0, 0, 0), sh_dir = mk3(0, 0, 0);
+        float sh_tmax = 0.0f, sh_c = 0.0f;
+        if (inst < 0) {
+            // miss: environment radiance (Sec. 3.1 samples the light reaching the pixel)
+            if (P.want_sig) sig = fnv(sig, 0xFFFFFFFFu);
+            if (sc.has_env) {
+                int row, col;
+                float st;
+                env_texel(sc, d, row, col, st);
+                if (P.want_sig) sig = fnv(sig, (uint32_t)(row * sc.env_w + col));
+                const float Le = __ldg(sc.env + (int64_t)row * sc.env_w + col);
+                float wgt = 1.0f;
+                if (depth > 0 && P.nee) wgt = P.mis ? power_heuristic(pdf_prev, fr.p_env * texel_pdf(sc, row, col, st)) : 0.0f;
+                L += beta * wgt * Le;
+            } else if (P.want_sig) {
+                sig = fnv(sig, 0xFFFFFFFEu);
+            }
+        } else {
+            const int tri = __float_as_int(hv.z);
+            const float4* tp = sc.tris + 3 * tri;
+            const float4 q0 = __ldg(tp), q1 = __ldg(tp + 1), q2 = __ldg(tp + 2);
+            const float4* ip = fr.inst + 7 * inst;
+            const float4 m0 = __ldg(ip), m1 = __ldg(ip + 1), m2 = __ldg(ip + 2);
+            const float4 i0 = __ldg(ip + 3), i1 = __ldg(ip + 4), i2 = __ldg(ip + 5);
+            const int ovr = __float_as_int(__ldg(ip + 6).y);
+            if (P.want_sig) {
+                sig = fnv(sig, (uint32_t)inst);
+                sig = fnv(sig, (uint32_t)__float_as_int(q0.w));
+            }
+            const float t = hv.x;
+            P0 = xyz(ro) + d * t;
+            const f3 e1 = xyz(q1) - xyz(q0), e2 = xyz(q2) - xyz(q0);
+            const f3 cr = cross3(e1, e2);
+            const f3 ng = norm3(xf_normal(i0, i1, i2, cr));
+            const f3 wo = d * -1.0f;
+            const int mat = ovr >= 0 ? ovr : __float_as_int(q1.w);
+            const float4 mv = __ldg(sc.mats + mat);
+            const int type = __float_as_int(mv.x);
+            const float alb = mv.y, rough = mv.z, emit = mv.w;
+            uint32_t flags = 0;
+            const float cos_o = dot3(ng, wo);
+            if (emit > 0.0f && cos_o > 0.0f) {
+                flags |= 1u;
+                float wgt = 1.0f;
+                if (depth > 0 && P.nee) {
+                    if (!P.mis) {
+                        wgt = 0.0f;
+                    } else {
+                        const f3 we1 = xf_vec(m0, m1, m2, e1), we2 = xf_vec(m0, m1, m2, e2);
+                        const f3 wc = cross3(we1, we2);
+                        const float area = 0.5f * sqrtf(dot3(wc, wc));
+                        const float pl = fr.p_area / ((float)fr.n_lights * area) * t * t / cos_o;
+                        wgt = power_heuristic(pdf_prev, pl);
+                    }
+                }
+                L += beta * wgt * emit;
+            }
+            if (depth < P.max_depth && alb > 0.0f) {
+                const f3 nn = cos_o < 0.0f ? ng * -1.0f : ng;
+                f3 tb, bt;
+                onb(nn, tb, bt);
+                const f3 wol = mk3(dot3(wo, tb), dot3(wo, bt), dot3(wo, nn));
+                const uint2 pk = make_uint2((uint32_t)w.pix_k[p].x, (uint32_t)w.pix_k[p].y);
+                // next-event estimation
+                if (P.nee && (sc.env_ok || fr.n_lights > 0)) {
+                    const uint4 x = philox4x32_10(make_uint4(pk.x, pk.y, (uint32_t)(depth + 1), 0u), fr.key0, fr.key1);
+                    const bool use_env = sc.env_ok && (fr.n_lights == 0 || u01(x.x) < 0.5f);
+                    f3 wi = mk3(0, 0, 0);
+                    float pl = 0.0f, Le = 0.0f, tmax = __int_as_float(0x7f800000);
+                    if (use_env) {
+                        float pdf;
+                        wi = env_sample(sc, u01(x.z), u01(x.w), pdf, Le);
+                        pl = fr.p_env * pdf;
+                    } else {
+                        const uint64_t mm = (uint64_t)(x.y >> 8);
+                        const int li = (int)((mm * (uint64_t)fr.n_lights) >> 24);
+                        const float4* lp = fr.lights + 4 * li;
+                        const float4 a0 = __ldg(lp), a1 = __ldg(lp + 1), a2 = __ldg(lp + 2), an = __ldg(lp + 3);
+                        const float su = sqrtf(u01(x.z));
+                        const float b0 = 1.0f - su, b1 = u01(x.w) * su, b2 = 1.0f - b0 - b1;
+                        const f3 Q = xyz(a0) * b0 + xyz(a1) * b1 + xyz(a2) * b2;
+                        const f3 dv = Q - P0;
+                        const float dist = sqrtf(dot3(dv, dv));
+                        wi = dv * (1.0f / dist);
+                        const float cl = -dot3(xyz(an), wi);
+                        if (cl > 0.0f) {
+                            pl = fr.p_area / ((float)fr.n_lights * a1.w) * dist * dist / cl;
+                            Le = a0.w;
+                        }
+                        tmax = dist - P.t_min;
+                    }
+                    if (pl > 0.0f && Le > 0.0f) {
+                        const f3 wil = mk3(dot3(wi, tb), dot3(wi, bt), dot3(wi, nn));
+                        float pb;
+                        const float f = bsdf_eval(type, alb, rough, wol, wil, &pb);
+                        if (f > 0.0f && wil.z > 0.0f) {
+                            flags |= 2u;
+                            const float wgt = P.mis ? power_heuristic(pl, pb) : 1.0f;
+                            sh_c = beta * f * wil.z * Le * wgt / pl;
+                            sh_dir = wi;
+                            sh_tmax = tmax;
+                            shadow = true;
+                        }
+                    }
+                }
+                // BSDF sampling of the continuation
+                const uint4 y = philox4x32_10(make_uint4(pk.x, pk.y, (uint32_t)(depth + 1), 1u), fr.key0, fr.key1);
+                const f3 wil = bsdf_sample(type, rough, wol, u01(y.x), u01(y.y));
+                float pb;
+                const float f = bsdf_eval(type, alb, rough, wol, wil, &pb);
+                if (f > 0.0f && pb > 0.0f && wil.z > 0.0f) {
+                    flags |= 8u;
+                    beta *= f * wil.z / pb;
+                    w.pdf_prev[p] = pb;
+                    wi_next = norm3(tb * wil.x + bt * wil.y + nn * wil.z);
+                    cont = true;
+                }
+            }
+            pflags = flags;
+        }
+        w.L[p] = L;
+        w.beta[p] = beta;
+        if (P.want_sig) {
+            w.sig[p] = sig;
+            w.pflags[p] = pflags;
+        }
+        const int si = warp_append(w.counters + 2, shadow);
+        if (shadow) {
+            w.sh_o[si] = make_float4(P0.x, P0.y, P0.z, __int_as_float(p));
+            w.sh_d[si] = make_float4(sh_dir.x, sh_dir.y, sh_dir.z, sh_tmax);
+            w.sh_c[si] = sh_c;
+        }
+        const int ni = warp_append(w.counters + (1 - cur), cont);
+        if (cont) {
+            w.ray_o[1 - cur][ni] = make_float4(P0.x, P0.y, P0.z, __int_as_float(p));
+            w.ray_d[1 - cur][ni] = make_float4(wi_next.x, wi_next.y, wi_next.z, __int_as_float(depth + 1));
+        }
+    }
+}
+
+// ------------------------------------------------------------------ shadow rays
+__global__ void __launch_bounds__(128) k_shadow(DevScene sc, DevFrame fr, DevParams P, Wave w, int32_t* err) {
+    const int32_t n = *(volatile int32_t*)(w.counters + 2);
+    int e = 0;
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float4 o = w.sh_o[i];
+        const float4 d = w.sh_d[i];
+        const int p = __float_as_int(o.w);
+        if (!occluded(sc, fr, xyz(o), xyz(d), P.t_min, d.w, &e)) {
+            w.L[p] += w.sh_c[i];
+            if (P.want_sig) w.pflags[p] |= 4u;
+        }
+    }
+    if (e) atomicOr(err, 1);
+}
+
+// ------------------------------------------------------------------ per-pixel statistics + test + requeue + events
+struct Moments {
+    float n, mean, m2;
+};
+__device__ __forceinline__ Moments chan(Moments a, Moments b) {
+    const float n = a.n + b.n;
+    if (n == 0.0f) return a;
+    const float dl = b.mean - a.mean;
+    Moments r;
+    r.n = n;
+    r.mean = a.mean + dl * (b.n / n);
+    r.m2 = a.m2 + b.m2 + dl * dl * (a.n * b.n / n);
+    return r;
+}
+
+__global__ void __launch_bounds__(256) k_stats(Wave w, StatsArgs A, const int32_t* __restrict__ queue, int64_t j0,
+                                               int64_t n_pix, int32_t* __restrict__ next_queue) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t j = warp0; j < n_pix; j += nwarps) {
+        const int32_t pix = __ldg(queue + j0 + j);
+        // per-lane Welford over the lane's samples of this batch
+        Moments m{0.0f, 0.0f, 0.0f};
+        int bad = 0;
+        const float* Lp = w.L + j * A.spp_r;
+        for (int s = lane; s < A.spp_r; s += 32) {
+            float Lv = Lp[s];
+            if (!isfinite(Lv)) {
+                Lv = 0.0f;
+                ++bad;
+            }
+            const float y = logf(Lv + A.eps);
+            m.n += 1.0f;
+            const float dl = y - m.mean;
+            m.mean += dl / m.n;
+            m.m2 += dl * (y - m.mean);
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            Moments o;
+            o.n = __shfl_xor_sync(0xffffffffu, m.n, off);
+            o.mean = __shfl_xor_sync(0xffffffffu, m.mean, off);
+            o.m2 = __shfl_xor_sync(0xffffffffu, m.m2, off);
+            // merge in a fixed lane order so every lane gets identical bits
+            m = (lane & off) ? chan(o, m) : chan(m, o);
+        }
+        bad = __reduce_add_sync(0xffffffffu, bad);
+        if (lane != 0) continue;
+        if (bad) atomicAdd(w.counters + 4, bad);
+        Moments c;
+        if (A.k_base == 0) {
+            c = m;
+        } else {
+            Moments prev{(float)A.cur.n[pix], A.cur.mean[pix], A.cur.m2[pix]};
+            c = chan(prev, m);
+        }
+        const int32_t n = (int32_t)c.n;
+        A.cur.n[pix] = n;
+        A.cur.mean[pix] = c.mean;
+        A.cur.m2[pix] = c.m2;
+        if (A.mode == MODE_REFERENCE) {
+            if (n >= A.spp_max) {
+                A.ref.n[pix] = n;
+                A.ref.mean[pix] = c.mean;
+                A.ref.m2[pix] = c.m2;
+            } else {
+                next_queue[atomicAdd(w.counters + 3, 1)] = pix;
+            }
+            continue;
+        }
+        const float ma = A.ref.mean[pix];
+        bool decided = n >= A.spp_max;
+        if (!decided && A.variant != VAR_UNIFORM) {
+            const float gap = fabsf(c.mean - ma);
+            if (A.variant == VAR_MEAN_ONLY) {
+                decided = gap < A.C;
+            } else {
+                const int32_t na = A.ref.n[pix];
+                const float va = na > 1 ? A.ref.m2[pix] / (float)(na - 1) : 0.0f;
+                const float vb = c.m2 / (float)(n - 1);
+                const float se2 = A.se_mode == SE_WELCH ? va / (float)na + vb / (float)n : (va + vb) / (float)n;
+                if (se2 == 0.0f) {
+                    decided = gap < A.C;
+                } else {
+                    const float t = (gap - A.C) / sqrtf(se2);
+                    const float tc = __ldg(A.tcrit + (n - A.spp_min) / A.spp_batch);
+                    decided = A.variant == VAR_TWO_TAILED ? (t < tc || t > -tc) : (t < tc);
+                }
+            }
+        }
+        if (!decided) {
+            next_queue[atomicAdd(w.counters + 3, 1)] = pix;
+            continue;
+        }
+        const float delta = c.mean - ma;
+        int8_t ev = 0;
+        if (fabsf(delta) > A.C) {
+            ev = delta > 0.0f ? 1 : -1;
+            A.ref.n[pix] = n;
+            A.ref.mean[pix] = c.mean;
+            A.ref.m2[pix] = c.m2;
+            atomicAdd(w.counters + (ev > 0 ? 5 : 6), 1);
+        }
+        if (n >= A.spp_max) atomicAdd(w.counters + 7, 1);
+        A.events[pix] = ev;
+        if (A.spp_out) A.spp_out[pix] = n;
+        if (A.mean_out) A.mean_out[pix] = c.mean;
+    }
+}
+
+// ------------------------------------------------------------------ tracePaths output
+__global__ void k_write_samples(Wave w, int64_t out0, int64_t n_paths, float* __restrict__ L_out,
+                                uint32_t* __restrict__ sig_out) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n_paths; p += (int64_t)gridDim.x * blockDim.x) {
+        L_out[out0 + p] = w.L[p];
+        if (sig_out) {
+            uint32_t s = w.sig[p];
+            const uint32_t pf = w.pflags[p];
+            if (pf != NO_FLAGS) s = fnv(s, pf);
+            sig_out[out0 + p] = s;
+        }
+    }
+}
+
+__global__ void k_iota(int32_t* q, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        q[i] = (int32_t)i;
+}
+
+// ------------------------------------------------------------------ launchers
+static int grid_for(int64_t work, int block, int sms, int per_sm) {
+    int64_t g = (work + block - 1) / block;
+    const int64_t cap = (int64_t)sms * per_sm;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+cudaError_t launch_raygen(const DevFrame& fr, const DevParams& P, const Wave& w, const int32_t* queue, int64_t j0,
+                          int32_t spp_r, int64_t k_base, int64_t n_paths, int cur, int sms, cudaStream_t st) {
+    k_raygen<<<grid_for(n_paths, 256, sms, 16), 256, 0, st>>>(fr, P, w, queue, j0, spp_r, k_base, n_paths, cur);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_extend(const DevScene& sc, const DevFrame& fr, float t_min, const Wave& w, int cur, int64_t max_n,
+                          int32_t* err, int sms, cudaStream_t st) {
+    k_extend<<<grid_for(max_n, 128, sms, 16), 128, 0, st>>>(sc, fr, t_min, w, cur, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_shade(const DevScene& sc, const DevFrame& fr, const DevParams& P, const Wave& w, int cur,
+                         int64_t max_n, int sms, cudaStream_t st) {
+    k_shade<<<grid_for(max_n, 128, sms, 16), 128, 0, st>>>(sc, fr, P, w, cur);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_shadow(const DevScene& sc, const DevFrame& fr, const DevParams& P, const Wave& w, int64_t max_n,
+                          int32_t* err, int sms, cudaStream_t st) {
+    k_shadow<<<grid_for(max_n, 128, sms, 16), 128, 0, st>>>(sc, fr, P, w, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stats(const Wave& w, const StatsArgs& A, const int32_t* queue, int64_t j0, int64_t n_pix,
+                         int32_t* next_queue, int sms, cudaStream_t st) {
+    k_stats<<<grid_for(n_pix * 32, 256, sms, 8), 256, 0, st>>>(w, A, queue, j0, n_pix, next_queue);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_write_samples(const Wave& w, int64_t out0, int64_t n_paths, float* L_out, uint32_t* sig_out,
+                                 int sms, cudaStream_t st) {
+    k_write_samples<<<grid_for(n_paths, 256, sms, 8), 256, 0, st>>>(w, out0, n_paths, L_out, sig_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_iota(int32_t* q, int64_t n, int sms, cudaStream_t st) {
+    k_iota<<<grid_for(n, 256, sms, 8), 256, 0, st>>>(q, n);
+    return cudaGetLastError();
+}
+
+}  // namespace mcev

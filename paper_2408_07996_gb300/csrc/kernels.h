@@ -1,0 +1,41 @@
+// kernels.h -- host-callable launchers of the renderer's kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "layout.h"
+
+namespace mcev {
+
+enum { MODE_REFERENCE = 0, MODE_DETECT = 1 };
+enum { VAR_ONE_TAILED = 0, VAR_TWO_TAILED = 1, VAR_MEAN_ONLY = 2, VAR_UNIFORM = 3 };
+enum { SE_PAPER = 0, SE_WELCH = 1 };
+
+struct StatsArgs {
+    PixStats cur, ref;
+    const float* tcrit;   // critical t per test round r, n = spp_min + r * spp_batch
+    int8_t* events;
+    int32_t* spp_out;
+    float* mean_out;
+    float eps, C;
+    int32_t spp_r;        // samples per pixel in this batch
+    int64_t k_base;       // samples taken before this batch
+    int32_t spp_min, spp_batch, spp_max;
+    int32_t mode, variant, se_mode;
+};
+
+cudaError_t launch_raygen(const DevFrame& fr, const DevParams& P, const Wave& w, const int32_t* queue, int64_t j0,
+                          int32_t spp_r, int64_t k_base, int64_t n_paths, int cur, int sms, cudaStream_t st);
+cudaError_t launch_extend(const DevScene& sc, const DevFrame& fr, float t_min, const Wave& w, int cur, int64_t max_n,
+                          int32_t* err, int sms, cudaStream_t st);
+cudaError_t launch_shade(const DevScene& sc, const DevFrame& fr, const DevParams& P, const Wave& w, int cur,
+                         int64_t max_n, int sms, cudaStream_t st);
+cudaError_t launch_shadow(const DevScene& sc, const DevFrame& fr, const DevParams& P, const Wave& w, int64_t max_n,
+                          int32_t* err, int sms, cudaStream_t st);
+cudaError_t launch_stats(const Wave& w, const StatsArgs& A, const int32_t* queue, int64_t j0, int64_t n_pix,
+                         int32_t* next_queue, int sms, cudaStream_t st);
+cudaError_t launch_write_samples(const Wave& w, int64_t out0, int64_t n_paths, float* L_out, uint32_t* sig_out,
+                                 int sms, cudaStream_t st);
+cudaError_t launch_iota(int32_t* q, int64_t n, int sms, cudaStream_t st);
+
+}  // namespace mcev

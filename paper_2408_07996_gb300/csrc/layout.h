@@ -1,0 +1,103 @@
+// layout.h -- device data layout of the renderer (host and device view).
+//
+// Everything the kernels read is plain arrays in HBM:
+//   BVH node (64 B, two child boxes in the parent so one node fetch tests
+//   both children):
+//     a = (L.lo.x, L.hi.x, L.lo.y, L.hi.y)   b = (R.lo.x, R.hi.x, R.lo.y, R.hi.y)
+//     c = (L.lo.z, L.hi.z, R.lo.z, R.hi.z)   d = (L, R, Lcount, Rcount)
+//   where a child >= 0 is an inner node and a child < 0 is a leaf holding
+//   triangles [~child, ~child + count) of the triangle array (TLAS leaves
+//   hold instance ids instead of triangles).
+//   Triangle (48 B): v0.xyz|prim, v1.xyz|material, v2.xyz|0 (object space,
+//   BVH leaf order; prim = index in the uploaded triangle list).
+//   Instance (112 B): M rows 0..2, Minv rows 0..2 (3x4 each, float4), then
+//   (blas root node, material override, 0, 0).
+//   Light (64 B): v0.xyz|Le, v1.xyz|area, v2.xyz|0, n.xyz|0 (world space).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#ifdef __CUDACC__
+#define MCEV_HD __host__ __device__
+#else
+#define MCEV_HD
+#endif
+
+// traversal stack entries per thread (TLAS + BLAS depth must fit)
+#define MCEV_STACK_HOST 96
+
+namespace mcev {
+
+struct Node {
+    float4 a, b, c;
+    int4 d;
+};
+
+enum { MAT_DIFFUSE = 0, MAT_GGX = 1 };
+
+struct DevScene {
+    const Node* nodes;        // BLAS nodes of every mesh
+    const float4* tris;       // 3 float4 per triangle, leaf order
+    const float4* mats;       // (type, albedo, rough, emit)
+    const float* env;         // [eh][ew] radiance
+    const float* env_marg;    // [eh + 1] row CDF
+    const float* env_cond;    // [eh][ew + 1] column CDFs
+    const float* env_tpdf;    // [eh][ew]: texel pdf numerator, pdf = tpdf / sin(theta)
+    int32_t env_w, env_h;
+    int32_t env_ok;           // environment present with positive total radiance
+    int32_t has_env;          // environment present (lookups on miss)
+};
+
+struct DevFrame {
+    const Node* tlas;         // TLAS nodes; leaves hold instance ids
+    const float4* inst;       // 7 float4 per instance
+    const float4* lights;     // 4 float4 per emissive triangle
+    int32_t n_inst, n_lights;
+    int32_t tlas_is_leaf;     // TLAS has a single instance: no TLAS traversal needed
+    int32_t pad0;
+    float eye[3], fwd[3], right[3], up[3];  // right, up prescaled by tan(fov/2)*aspect
+    uint32_t key0, key1;      // Philox key
+    float p_env, p_area;      // NEE light-type selection probabilities
+};
+
+// Per-render settings, passed by value to the kernels.
+struct DevParams {
+    int32_t width, height;
+    int32_t max_depth;
+    int32_t nee, mis;
+    float eps;
+    float t_min;
+    int32_t want_sig;         // maintain the decision signature
+};
+
+// Wavefront buffers of one chunk (capacity = `cap` paths).
+struct Wave {
+    // per path slot p
+    float* beta;
+    float* L;
+    float* pdf_prev;
+    uint32_t* sig;
+    uint32_t* pflags;         // pending flags of the last vertex (0xFFFFFFFF = none)
+    int2* pix_k;              // (pixel, sample index)
+    // ray queues (ping-pong) and hits, per queue slot
+    float4* ray_o[2];         // xyz origin, w = path slot (int bits)
+    float4* ray_d[2];         // xyz direction, w = depth (int bits)
+    float4* hit;              // t, instance, leaf-order triangle, 0   (inst < 0: miss)
+    // shadow rays
+    float4* sh_o;             // xyz origin, w = path slot
+    float4* sh_d;             // xyz direction, w = t_max
+    float* sh_c;              // unoccluded contribution
+    // device counters: [0],[1] ray queue sizes, [2] shadow count, [3] pixel queue
+    // size, [4] non-finite path values, [5] events +, [6] events -, [7] at cap
+    int32_t* counters;
+    int64_t cap;
+};
+
+// Per-pixel statistics (SoA): count, mean and M2 of ln(L + eps).
+struct PixStats {
+    int32_t* n;
+    float* mean;
+    float* m2;
+};
+
+}  // namespace mcev

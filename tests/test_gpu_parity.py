@@ -1,0 +1,198 @@
+"""GPU (CUDA path through the C ABI) vs the FP64 oracle on identical Philox
+streams.  Tolerances: per-pixel mean ln(L + eps) within 1e-4 absolute at equal
+sample counts; event maps identical except at pixels whose t lies within
+1e-3 of the critical value (or whose mean gap lies within 1e-5 of C), and
+except pixels where a sample's discrete decisions (hit triangle, visibility,
+texel) differ between FP32 and FP64 geometry, which are counted."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import scenegen as sg
+from parity import per_sample, renderer_for, summary
+
+pytestmark = pytest.mark.gpu
+
+MEAN_TOL = 1e-4      # per-pixel mean ln L, absolute (spec tolerance)
+T_BAND = 1e-3        # |t - t_crit| band where FP32/FP64 decisions may differ
+C_BAND = 1e-5        # | |gap| - C | band
+SAMPLE_MISMATCH = 2e-3   # max fraction of samples with different discrete decisions
+
+
+@pytest.fixture(scope="module")
+def cornell():
+    w = sg.workload("cornell64")
+    return w, O.OracleScene(w.scene)
+
+
+# ---------------------------------------------------------------- closed forms on the GPU
+
+def test_gpu_white_furnace_exact():
+    sc = sg.furnace_sphere(0.5, 1.0)
+    w = sg.Workload("furnace", sc, 16, 16, [0.0, 1.0], spp_min=16, spp_batch=16, spp_max=64, C=0.2,
+                    alpha=0.05, max_depth=4, nee=0, mis=0)
+    r = renderer_for(w)
+    L, _ = r.trace_samples(0.0, torch.arange(256, dtype=torch.int32), 0, 32)
+    np.testing.assert_allclose(L.cpu().numpy(), 1.9375, rtol=2e-6)
+    r.close()
+
+
+def test_gpu_plane_and_empty_scene_exact():
+    sc = sg.plane_under_env(0.5, 2.0)
+    w = sg.Workload("plane", sc, 16, 16, [0.0, 1.0], spp_min=16, spp_batch=16, spp_max=64, C=0.2,
+                    alpha=0.05, max_depth=3, nee=0, mis=0)
+    r = renderer_for(w)
+    L, _ = r.trace_samples(0.0, torch.arange(256, dtype=torch.int32), 0, 16)
+    np.testing.assert_allclose(L.cpu().numpy(), 1.0, rtol=2e-6)
+    r.close()
+    w.scene = sg.empty_env(3.0)
+    r = renderer_for(w)
+    L, _ = r.trace_samples(0.0, torch.arange(256, dtype=torch.int32), 0, 4)
+    np.testing.assert_array_equal(L.cpu().numpy(), 3.0)
+    r.close()
+
+
+# ---------------------------------------------------------------- per-sample parity
+
+@pytest.mark.parametrize("t", [0.0, 1.0])
+def test_cornell_per_sample_parity(cornell, t):
+    w, osc = cornell
+    r = renderer_for(w, wavefront=5000)          # several chunks with a ragged tail
+    pix = np.arange(0, 4096, 3)                  # 1366 pixels
+    ps = per_sample(r, osc, O.params_of(w), t, pix, 5, 37, w.eps)
+    s = summary(ps)
+    print("cornell per-sample", t, s)
+    assert s["mismatch"] <= SAMPLE_MISMATCH
+    assert s["max_dy"] < 1e-3
+    # per-pixel means over pixels whose every sample made the same decisions
+    full = ps["match"].all(axis=1)
+    dm = np.abs(ps["yg"].mean(1) - ps["yo"].mean(1))[full]
+    assert dm.max() < MEAN_TOL
+    r.close()
+
+
+# ---------------------------------------------------------------- Alg. 1 frame parity
+
+def _event_parity(r, osc, w, det, t0, t1, H, W, p):
+    out = r.render_events(t0, t1, w.C, w.alpha, w.spp_batch, w.spp_max)
+    ev = out["events"].cpu().numpy().reshape(-1)
+    n = out["spp"].cpu().numpy().reshape(-1)
+    mean = out["mean"].cpu().numpy().reshape(-1)
+    pix = np.arange(H * W, dtype=np.int32)
+    ref = O.render_events(osc, p, det, t0, t1, pix)
+    # samples drawn by either side, checked for equal discrete decisions
+    k_t1 = int(max(n.max(), ref["n"].max()))
+    m0 = per_sample(r, osc, p, t0, pix, 0, w.spp_max, w.eps)["match"].all(1)
+    m1 = per_sample(r, osc, p, t1, pix, 0, k_t1, w.eps)["match"]
+    kk = np.arange(k_t1)[None, :]
+    m1 = np.where(kk < np.maximum(n, ref["n"])[:, None], m1, True).all(1)
+    topo_ok = m0 & m1
+    band = (ref["margin_t"] < T_BAND) | (ref["margin_c"] < C_BAND)
+    keep = topo_ok & ~band
+    bad_ev = keep & (ev != ref["events"])
+    bad_n = keep & (n != ref["n"])
+    same_n = keep & (n == ref["n"])
+    dmean = np.abs(mean - ref["mean"])[same_n]
+    return dict(out=out, ref=ref, keep=keep, topo_ok=topo_ok, band=band, bad_ev=bad_ev, bad_n=bad_n,
+                dmean=dmean, ev=ev, n=n)
+
+
+def test_cornell_event_frame_parity(cornell):
+    w, osc = cornell
+    r = renderer_for(w)
+    res = _event_parity(r, osc, w, O.detect_of(w), 0.0, 1.0, w.height, w.width, O.params_of(w))
+    print("cornell events: kept %.4f, topo-excluded %.4f, band-excluded %.4f, events %d/%d, mean n %.1f" % (
+        res["keep"].mean(), 1 - res["topo_ok"].mean(), res["band"].mean(), (res["ev"] != 0).sum(),
+        (res["ref"]["events"] != 0).sum(), res["n"].mean()))
+    assert res["bad_ev"].sum() == 0
+    assert res["bad_n"].sum() == 0
+    assert res["dmean"].max() < MEAN_TOL
+    # a pixel is set aside when any of its ~2*spp samples took a different
+    # discrete decision; with per-sample rate q that is ~1-(1-q)^(2 spp)
+    q = SAMPLE_MISMATCH
+    assert 1 - res["topo_ok"].mean() <= 1 - (1 - q) ** (2 * w.spp_max)
+    assert res["band"].mean() < 0.01
+    st = res["out"]["stats"]
+    assert st["events_pos"] + st["events_neg"] == int((res["ev"] != 0).sum())
+    assert st["paths"] == int(res["n"].sum())
+    r.close()
+
+
+@pytest.mark.parametrize("variant", [O.UNIFORM, O.TWO_TAILED, O.MEAN_ONLY])
+def test_cornell_variant_parity(cornell, variant):
+    w, osc = cornell
+    r = renderer_for(w, variant=variant)
+    res = _event_parity(r, osc, w, O.detect_of(w, variant=variant), 0.0, 1.0, w.height, w.width,
+                        O.params_of(w))
+    assert res["bad_ev"].sum() == 0 and res["bad_n"].sum() == 0
+    assert res["dmean"].max() < MEAN_TOL
+    if variant == O.UNIFORM:
+        assert (res["n"] == w.spp_max).all()
+    r.close()
+
+
+def test_second_frame_reuses_reference(cornell):
+    # frames (0,1) then (1,2): the reference carried over equals the oracle's
+    w, osc = cornell
+    sc = sg.cornell_box(shift=0.02)
+    sc3 = sg.Scene(sc.vertices, sc.triangles, sc.tri_material, sc.mesh_ranges, sc.inst_mesh,
+                   sc.inst_material, np.array([0.0, 1.0, 2.0]), np.repeat(sc.inst_xform[:1], 3, 0),
+                   np.stack([sc.cam_eye[0], sc.cam_eye[1], sc.cam_eye[1] + [0.02, 0, 0]]),
+                   np.stack([sc.cam_target[0], sc.cam_target[1], sc.cam_target[1] + [0.02, 0, 0]]),
+                   np.repeat(sc.cam_up[:1], 3, 0), sc.fov_deg, sc.mat_type, sc.mat_albedo,
+                   sc.mat_rough, sc.mat_emit, sc.env)
+    w3 = sg.workload("cornell64")
+    w3.scene = sc3
+    osc3 = O.OracleScene(sc3)
+    r = renderer_for(w3)
+    p, det = O.params_of(w3), O.detect_of(w3)
+    pix = np.arange(w3.width * w3.height, dtype=np.int32)
+    r.render_events(0.0, 1.0, w3.C, w3.alpha, w3.spp_batch, w3.spp_max)
+    o1 = O.render_events(osc3, p, det, 0.0, 1.0, pix)
+    out2 = r.render_events(1.0, 2.0, w3.C, w3.alpha, w3.spp_batch, w3.spp_max)
+    assert out2["stats"]["ref_paths"] == 0
+    o2 = O.render_events(osc3, p, det, 1.0, 2.0, pix, ref=o1["ref"])
+    ev = out2["events"].cpu().numpy().reshape(-1)
+    band = (o2["margin_t"] < T_BAND) | (o2["margin_c"] < C_BAND) | (o1["margin_t"] < T_BAND) | (o1["margin_c"] < C_BAND)
+    agree = (ev == o2["events"]) | band
+    assert agree.mean() > 0.97
+    r.close()
+
+
+def test_state_roundtrip_and_determinism(cornell):
+    w, _ = cornell
+    r = renderer_for(w)
+    a = r.render_events(0.0, 1.0, w.C, w.alpha, w.spp_batch, w.spp_max)
+    st = r.get_state().clone()
+    b = r.render_events(1.0, 2.0, w.C, w.alpha, w.spp_batch, w.spp_max)
+    r.set_state(st)
+    c = r.render_events(1.0, 2.0, w.C, w.alpha, w.spp_batch, w.spp_max)
+    for k in ("events", "spp", "mean"):
+        assert torch.equal(b[k], c[k])
+    r2 = renderer_for(w)
+    a2 = r2.render_events(0.0, 1.0, w.C, w.alpha, w.spp_batch, w.spp_max)
+    for k in ("events", "spp", "mean"):
+        assert torch.equal(a[k], a2[k])
+    r.close()
+    r2.close()
+
+
+def test_errors_are_statuses_not_crashes():
+    from paper_2408_07996_gb300 import McevError
+    from paper_2408_07996_gb300.api import Renderer
+    r = Renderer(8, 8)
+    with pytest.raises(McevError, match="STATE"):
+        r.render_events(0.0, 1.0, 0.2, 0.05, 16, 256)
+    w = sg.workload("cornell64")
+    r.upload(w.scene)
+    with pytest.raises(McevError, match="ARG"):
+        r.render_events(0.0, 1.0, 0.2, 1.5, 16, 256)
+    with pytest.raises(McevError, match="ARG"):
+        r.set_params(spp_min=1)
+    bad = sg.cornell_box()
+    bad.triangles = bad.triangles.copy()
+    bad.triangles[0, 0] = 10 ** 6
+    with pytest.raises(McevError, match="ARG"):
+        r.upload(bad)
+    r.close()
