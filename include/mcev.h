@@ -104,7 +104,13 @@ typedef struct {
     int32_t se_mode;    /* MCEV_SE_PAPER or MCEV_SE_WELCH */
     uint64_t seed;      /* Philox key seed */
     int64_t wavefront;  /* max paths in flight per chunk; 0 = library default */
+    int32_t profile;    /* 1: time every kernel launch with CUDA events (mcev_stats.kernel_ms) */
+    int32_t reserved;   /* must be 0 */
 } mcev_params;
+
+/* kernel classes reported in mcev_stats */
+enum { MCEV_K_RAYGEN = 0, MCEV_K_EXTEND = 1, MCEV_K_SHADE = 2, MCEV_K_SHADOW = 3, MCEV_K_STATS = 4,
+       MCEV_K_CLASSES = 5 };
 
 /* Per-call counters (mcev_render_events, optional). */
 typedef struct {
@@ -116,6 +122,16 @@ typedef struct {
     int64_t pixels_at_cap;  /* pixels that used spp_max samples */
     int64_t nonfinite;      /* path values that were not finite and counted as 0 */
     double gpu_ms;          /* device time of the call (CUDA events) */
+    /* traversal work: BVH nodes fetched (each tests two child boxes) and
+     * ray/triangle tests, for closest-hit and for shadow (any-hit) rays */
+    int64_t nodes_closest, tris_closest, nodes_shadow, tris_shadow;
+    int64_t rays_closest, rays_shadow;
+    /* per kernel class (MCEV_K_*): launches, and summed device time in ms
+     * when mcev_params.profile = 1 (else 0) */
+    int32_t kernel_count[MCEV_K_CLASSES];
+    int32_t reserved;
+    double kernel_ms[MCEV_K_CLASSES];
+    int64_t h2d_bytes, d2h_bytes;   /* host<->device copies made by the call */
 } mcev_stats;
 
 /* Creates a context on CUDA device `device` for width x height images.

@@ -41,7 +41,7 @@ class Params(C.Structure):
     _fields_ = [
         ("eps", C.c_float), ("t_min", C.c_float), ("max_depth", C.c_int32), ("nee", C.c_int32),
         ("mis", C.c_int32), ("spp_min", C.c_int32), ("variant", C.c_int32), ("se_mode", C.c_int32),
-        ("seed", C.c_uint64), ("wavefront", C.c_int64),
+        ("seed", C.c_uint64), ("wavefront", C.c_int64), ("profile", C.c_int32), ("reserved", C.c_int32),
     ]
 
 
@@ -50,10 +50,18 @@ class Stats(C.Structure):
         ("paths", C.c_int64), ("ref_paths", C.c_int64), ("rounds", C.c_int32),
         ("kernel_launches", C.c_int32), ("events_pos", C.c_int64), ("events_neg", C.c_int64),
         ("pixels_at_cap", C.c_int64), ("nonfinite", C.c_int64), ("gpu_ms", C.c_double),
+        ("nodes_closest", C.c_int64), ("tris_closest", C.c_int64), ("nodes_shadow", C.c_int64),
+        ("tris_shadow", C.c_int64), ("rays_closest", C.c_int64), ("rays_shadow", C.c_int64),
+        ("kernel_count", C.c_int32 * 5), ("reserved", C.c_int32), ("kernel_ms", C.c_double * 5),
+        ("h2d_bytes", C.c_int64), ("d2h_bytes", C.c_int64),
     ]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {}
+        for k, _ in self._fields_:
+            v = getattr(self, k)
+            d[k] = list(v) if hasattr(v, "__len__") else v
+        return d
 
 
 # every symbol include/mcev.h declares, with its ctypes signature

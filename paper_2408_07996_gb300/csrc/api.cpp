@@ -57,6 +57,13 @@ struct mcev_ctx {
     std::string err;
     mcev_params params{};
     int launches = 0;
+    int32_t kcount[MCEV_K_CLASSES] = {0};
+    double kms[MCEV_K_CLASSES] = {0};
+    int64_t h2d = 0, d2h = 0;
+    // profile mode: event pairs around launches, drained at round ends
+    std::vector<cudaEvent_t> evpool;
+    std::vector<int> evclass;
+    size_t evused = 0;
 
     // host copy of the scene (needed per frame)
     bool have_scene = false;
@@ -162,7 +169,41 @@ mcev_status upload(mcev_ctx* ctx, DevBuf& b, const void* src, size_t bytes) {
     if (bytes) {
         CU(cudaMemcpyAsync(b.ptr, src, bytes, cudaMemcpyHostToDevice, ctx->stream));
         CU(cudaStreamSynchronize(ctx->stream));
+        ctx->h2d += (int64_t)bytes;
     }
+    return MCEV_OK;
+}
+
+// ---------------------------------------------------------------- per-kernel timing (profile mode)
+mcev_status drain_events(mcev_ctx* ctx) {
+    if (ctx->evused == 0) return MCEV_OK;
+    CU(cudaEventSynchronize(ctx->evpool[ctx->evused - 1]));
+    for (size_t i = 0; i + 1 < ctx->evused; i += 2) {
+        float ms = 0.0f;
+        CU(cudaEventElapsedTime(&ms, ctx->evpool[i], ctx->evpool[i + 1]));
+        ctx->kms[ctx->evclass[i / 2]] += ms;
+    }
+    ctx->evused = 0;
+    return MCEV_OK;
+}
+
+mcev_status ev_mark(mcev_ctx* ctx, int cls, bool start) {
+    if (!ctx->params.profile) return MCEV_OK;
+    if (start && ctx->evused + 2 > ctx->evpool.size()) {
+        if (ctx->evpool.size() >= 8192) {
+            ST(drain_events(ctx));
+        } else {
+            const size_t grow = ctx->evpool.size() ? ctx->evpool.size() : 256;
+            for (size_t i = 0; i < grow; ++i) {
+                cudaEvent_t e;
+                CU(cudaEventCreate(&e));
+                ctx->evpool.push_back(e);
+            }
+            ctx->evclass.resize(ctx->evpool.size() / 2);
+        }
+    }
+    if (start) ctx->evclass[ctx->evused / 2] = cls;
+    CU(cudaEventRecord(ctx->evpool[ctx->evused++], ctx->stream));
     return MCEV_OK;
 }
 
@@ -416,6 +457,7 @@ mcev_status frame_setup(mcev_ctx* ctx, double t, int slot) {
     CU(cudaStreamSynchronize(ctx->stream));
     CU(cudaMemcpyAsync(fr.buf.ptr, host.data(), total, cudaMemcpyHostToDevice, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
+    ctx->h2d += (int64_t)total;
     char* base = (char*)fr.buf.ptr;
     DevFrame& d = fr.dev;
     d.tlas = (const Node*)base;
@@ -546,12 +588,15 @@ DevParams dev_params(const mcev_ctx* ctx, bool want_sig) {
     return P;
 }
 
-#define LAUNCH(expr)                                                                                  \
+#define LAUNCH(cls, expr)                                                                             \
     do {                                                                                              \
+        ST(ev_mark(ctx, cls, true));                                                                  \
         cudaError_t e_ = (expr);                                                                      \
         ++ctx->launches;                                                                              \
+        ++ctx->kcount[cls];                                                                           \
         if (e_ != cudaSuccess)                                                                        \
             return fail(ctx, MCEV_ERR_CUDA, "launch %s failed: %s", #expr, cudaGetErrorString(e_));   \
+        ST(ev_mark(ctx, cls, false));                                                                 \
     } while (0)
 
 // one chunk of n_paths = nj * spp_r paths through every bounce
@@ -559,13 +604,13 @@ mcev_status trace_chunk(mcev_ctx* ctx, const Frame& fr, const DevParams& P, cons
                         int32_t spp_r, int64_t k_base, int64_t n_paths) {
     const Wave& w = ctx->wave;
     int32_t* err = ctx->wave.counters + 15;
-    LAUNCH(launch_raygen(fr.dev, P, w, queue, j0, spp_r, k_base, n_paths, 0, ctx->sms, ctx->stream));
+    LAUNCH(MCEV_K_RAYGEN, launch_raygen(fr.dev, P, w, queue, j0, spp_r, k_base, n_paths, 0, ctx->sms, ctx->stream));
     int cur = 0;
     for (int depth = 0; depth <= P.max_depth; ++depth) {
-        LAUNCH(launch_extend(ctx->dsc, fr.dev, P.t_min, w, cur, n_paths, err, ctx->sms, ctx->stream));
-        LAUNCH(launch_shade(ctx->dsc, fr.dev, P, w, cur, n_paths, ctx->sms, ctx->stream));
+        LAUNCH(MCEV_K_EXTEND, launch_extend(ctx->dsc, fr.dev, P.t_min, w, cur, n_paths, err, ctx->sms, ctx->stream));
+        LAUNCH(MCEV_K_SHADE, launch_shade(ctx->dsc, fr.dev, P, w, cur, n_paths, ctx->sms, ctx->stream));
         if (depth < P.max_depth && P.nee)
-            LAUNCH(launch_shadow(ctx->dsc, fr.dev, P, w, n_paths, err, ctx->sms, ctx->stream));
+            LAUNCH(MCEV_K_SHADOW, launch_shadow(ctx->dsc, fr.dev, P, w, n_paths, err, ctx->sms, ctx->stream));
         cur ^= 1;
     }
     return MCEV_OK;
@@ -577,7 +622,7 @@ mcev_status trace_chunk(mcev_ctx* ctx, const Frame& fr, const DevParams& P, cons
 mcev_status run_rounds(mcev_ctx* ctx, const Frame& fr, StatsArgs A, int64_t* paths_out, int32_t* rounds_out) {
     const int64_t npix = (int64_t)ctx->W * ctx->H;
     const DevParams P = dev_params(ctx, false);
-    LAUNCH(launch_iota(ctx->queue[0], npix, ctx->sms, ctx->stream));
+    LAUNCH(MCEV_K_STATS, launch_iota(ctx->queue[0], npix, ctx->sms, ctx->stream));
     int64_t Q = npix, n_done = 0, paths = 0;
     int rounds = 0, qi = 0;
     int32_t h_count = 0;
@@ -591,13 +636,15 @@ mcev_status run_rounds(mcev_ctx* ctx, const Frame& fr, StatsArgs A, int64_t* pat
         for (int64_t j0 = 0; j0 < Q; j0 += per_chunk) {
             const int64_t nj = std::min(per_chunk, Q - j0);
             ST(trace_chunk(ctx, fr, P, ctx->queue[qi], j0, spp_r, n_done, nj * spp_r));
-            LAUNCH(launch_stats(ctx->wave, A, ctx->queue[qi], j0, nj, ctx->queue[qi ^ 1], ctx->sms, ctx->stream));
+            LAUNCH(MCEV_K_STATS, launch_stats(ctx->wave, A, ctx->queue[qi], j0, nj, ctx->queue[qi ^ 1], ctx->sms, ctx->stream));
         }
         paths += Q * spp_r;
         n_done += spp_r;
         ++rounds;
         CU(cudaMemcpyAsync(&h_count, ctx->wave.counters + 3, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
         CU(cudaStreamSynchronize(ctx->stream));
+        ctx->d2h += (int64_t)sizeof(int32_t);
+        ST(drain_events(ctx));
         Q = h_count;
         qi ^= 1;
         if (n_done >= A.spp_max && Q != 0)
@@ -606,6 +653,16 @@ mcev_status run_rounds(mcev_ctx* ctx, const Frame& fr, StatsArgs A, int64_t* pat
     if (paths_out) *paths_out = paths;
     if (rounds_out) *rounds_out = rounds;
     return MCEV_OK;
+}
+
+void reset_call_counters(mcev_ctx* ctx) {
+    ctx->launches = 0;
+    for (int i = 0; i < MCEV_K_CLASSES; ++i) {
+        ctx->kcount[i] = 0;
+        ctx->kms[i] = 0.0;
+    }
+    ctx->h2d = ctx->d2h = 0;
+    ctx->evused = 0;
 }
 
 mcev_status check_ready(mcev_ctx* ctx) {
@@ -683,6 +740,7 @@ void mcev_destroy(mcev_ctx* ctx) {
                       &ctx->d_tpdf, &ctx->frames[0].buf, &ctx->frames[1].buf, &ctx->d_wave, &ctx->d_counters,
                       &ctx->d_pix, &ctx->d_tcrit};
     for (DevBuf* b : bufs) dev_free(ctx, *b);
+    for (cudaEvent_t e : ctx->evpool) cudaEventDestroy(e);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
     delete ctx;
@@ -837,6 +895,7 @@ mcev_status mcev_set_params(mcev_ctx* ctx, const mcev_params* p) {
     const bool shape = p->eps != ctx->params.eps || p->t_min != ctx->params.t_min ||
                        p->max_depth != ctx->params.max_depth || p->nee != ctx->params.nee || p->mis != ctx->params.mis;
     ctx->params = *p;
+    if (p->reserved != 0) return fail(ctx, MCEV_ERR_ARG, "reserved field must be 0");
     if (reseed || shape) {
         ctx->ref_valid = false;
         for (auto& f : ctx->frames) f.valid = false;
@@ -847,7 +906,7 @@ mcev_status mcev_set_params(mcev_ctx* ctx, const mcev_params* p) {
 mcev_status mcev_render_reference(mcev_ctx* ctx, double t0, int32_t spp) {
     ST(check_ready(ctx));
     if (spp < 2) return fail(ctx, MCEV_ERR_ARG, "spp must be >= 2");
-    ctx->launches = 0;
+    reset_call_counters(ctx);
     return do_reference(ctx, t0, spp, nullptr);
 }
 
@@ -858,14 +917,14 @@ mcev_status mcev_render_events(mcev_ctx* ctx, double t0, double t1, float C, flo
     if (!events_out) return fail(ctx, MCEV_ERR_ARG, "events_out is required");
     if (!(C >= 0.0f) || !(alpha > 0.0f && alpha < 1.0f) || spp_batch < 1 || spp_max < ctx->params.spp_min)
         return fail(ctx, MCEV_ERR_ARG, "need C >= 0, 0 < alpha < 1, spp_batch >= 1, spp_max >= spp_min");
-    ctx->launches = 0;
+    reset_call_counters(ctx);
+    CU(cudaMemsetAsync(ctx->wave.counters + 4, 0, 60 * sizeof(int32_t), ctx->stream));
     CU(cudaEventRecord(ctx->ev0, ctx->stream));
     int64_t ref_paths = 0, paths = 0;
     int32_t rounds = 0;
     if (!ctx->ref_valid || ctx->ref_time != t0) ST(do_reference(ctx, t0, spp_max, &ref_paths));
     ST(frame_setup(ctx, t1, 1));
     ST(ensure_tcrit(ctx, alpha, ctx->params.variant, ctx->params.spp_min, spp_batch, spp_max));
-    CU(cudaMemsetAsync(ctx->wave.counters + 4, 0, 12 * sizeof(int32_t), ctx->stream));
     StatsArgs A{};
     A.cur = ctx->cur;
     A.ref = ctx->ref;
@@ -885,12 +944,16 @@ mcev_status mcev_render_events(mcev_ctx* ctx, double t0, double t1, float C, flo
     ctx->ref_valid = true;
     ctx->ref_time = t1;
     CU(cudaEventRecord(ctx->ev1, ctx->stream));
+    ST(drain_events(ctx));
     if (stats_out) {
-        int32_t c[16];
+        int32_t c[64];
         CU(cudaMemcpyAsync(c, ctx->wave.counters, sizeof c, cudaMemcpyDeviceToHost, ctx->stream));
         CU(cudaStreamSynchronize(ctx->stream));
+        ctx->d2h += (int64_t)sizeof c;
         float ms = 0.0f;
         CU(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
+        uint64_t u[16];
+        std::memcpy(u, c + 32, sizeof u);
         std::memset(stats_out, 0, sizeof *stats_out);
         stats_out->paths = paths;
         stats_out->ref_paths = ref_paths;
@@ -901,6 +964,18 @@ mcev_status mcev_render_events(mcev_ctx* ctx, double t0, double t1, float C, flo
         stats_out->events_neg = c[6];
         stats_out->pixels_at_cap = c[7];
         stats_out->gpu_ms = ms;
+        stats_out->nodes_closest = (int64_t)u[0];
+        stats_out->tris_closest = (int64_t)u[1];
+        stats_out->nodes_shadow = (int64_t)u[2];
+        stats_out->tris_shadow = (int64_t)u[3];
+        stats_out->rays_closest = (int64_t)u[4];
+        stats_out->rays_shadow = (int64_t)u[5];
+        for (int i = 0; i < MCEV_K_CLASSES; ++i) {
+            stats_out->kernel_count[i] = ctx->kcount[i];
+            stats_out->kernel_ms[i] = ctx->kms[i];
+        }
+        stats_out->h2d_bytes = ctx->h2d;
+        stats_out->d2h_bytes = ctx->d2h;
         if (c[15]) return fail(ctx, MCEV_ERR_STATE, "traversal stack overflow");
     }
     return MCEV_OK;
@@ -912,14 +987,14 @@ mcev_status mcev_trace_samples(mcev_ctx* ctx, double t, const int32_t* pixels, i
     if (!pixels || !L_out || n_pix < 0 || k0 < 0 || count < 1 || k0 + count > ((int64_t)1 << 32))
         return fail(ctx, MCEV_ERR_ARG, "bad trace_samples arguments");
     if (n_pix == 0) return MCEV_OK;
-    ctx->launches = 0;
+    reset_call_counters(ctx);
     ST(frame_setup(ctx, t, 0));
     const DevParams P = dev_params(ctx, sig_out != nullptr);
     const int64_t per_chunk = std::max<int64_t>(1, ctx->wave.cap / count);
     for (int64_t j0 = 0; j0 < n_pix; j0 += per_chunk) {
         const int64_t nj = std::min(per_chunk, n_pix - j0);
         ST(trace_chunk(ctx, ctx->frames[0], P, pixels, j0, count, k0, nj * count));
-        LAUNCH(launch_write_samples(ctx->wave, j0 * count, nj * count, L_out, sig_out, ctx->sms, ctx->stream));
+        LAUNCH(MCEV_K_STATS, launch_write_samples(ctx->wave, j0 * count, nj * count, L_out, sig_out, ctx->sms, ctx->stream));
     }
     return MCEV_OK;
 }

@@ -285,17 +285,19 @@ __device__ __forceinline__ bool better_hit(float t, int inst, int prim, const Hi
 
 // BLAS closest hit of an object-space ray; updates h
 __device__ __forceinline__ void blas_closest(const DevScene& sc, int root, int inst, const WRay& r,
-                                             float tmin, Hit& h, int* stack, int base, int* err) {
+                                             float tmin, Hit& h, int* stack, int base, int* err, int2& work) {
     int sp = base;
     int node = root;
     while (true) {
         const Node n = load_node(sc.nodes, node);
+        work.x += 1;
         float tl, tr;
         const int m = node_hits(r, n, tmin, h.t, tl, tr);
         int next = -0x7fffffff;
         // leaves: test triangles immediately
         if ((m & 1) && n.d.x < 0) {
             const int first = ~n.d.x;
+            work.y += n.d.z;
             for (int i = 0; i < n.d.z; ++i) {
                 const float4* tp = sc.tris + 3 * (first + i);
                 const float4 p0 = __ldg(tp), p1 = __ldg(tp + 1), p2 = __ldg(tp + 2);
@@ -307,6 +309,7 @@ __device__ __forceinline__ void blas_closest(const DevScene& sc, int root, int i
         }
         if ((m & 2) && n.d.y < 0) {
             const int first = ~n.d.y;
+            work.y += n.d.w;
             for (int i = 0; i < n.d.w; ++i) {
                 const float4* tp = sc.tris + 3 * (first + i);
                 const float4 p0 = __ldg(tp), p1 = __ldg(tp + 1), p2 = __ldg(tp + 2);
@@ -338,11 +341,12 @@ __device__ __forceinline__ void blas_closest(const DevScene& sc, int root, int i
 }
 
 __device__ __forceinline__ bool blas_any(const DevScene& sc, int root, const WRay& r, float tmin, float tmax,
-                                         int* stack, int base, int* err) {
+                                         int* stack, int base, int* err, int2& work) {
     int sp = base;
     int node = root;
     while (true) {
         const Node n = load_node(sc.nodes, node);
+        work.x += 1;
         float tl, tr;
         const int m = node_hits(r, n, tmin, tmax, tl, tr);
         for (int side = 0; side < 2; ++side) {
@@ -352,6 +356,7 @@ __device__ __forceinline__ bool blas_any(const DevScene& sc, int root, const WRa
                 const int first = ~child;
                 for (int i = 0; i < cnt; ++i) {
                     const float4* tp = sc.tris + 3 * (first + i);
+                    work.y += 1;
                     if (tri_hit(r, __ldg(tp), __ldg(tp + 1), __ldg(tp + 2), tmin, tmax) >= 0.0f) return true;
                 }
             }
@@ -385,7 +390,8 @@ __device__ __forceinline__ WRay object_ray(const DevFrame& fr, int inst, f3 o, f
 }
 
 // world-space closest hit over the two-level hierarchy
-__device__ __forceinline__ Hit closest_hit(const DevScene& sc, const DevFrame& fr, f3 o, f3 d, float tmin, int* err) {
+__device__ __forceinline__ Hit closest_hit(const DevScene& sc, const DevFrame& fr, f3 o, f3 d, float tmin, int* err,
+                                           int2& work) {
     Hit h;
     h.t = __int_as_float(0x7f800000);
     h.inst = -1;
@@ -396,7 +402,7 @@ __device__ __forceinline__ Hit closest_hit(const DevScene& sc, const DevFrame& f
     if (fr.tlas_is_leaf) {
         int root;
         const WRay r = object_ray(fr, 0, o, d, root);
-        blas_closest(sc, root, 0, r, tmin, h, stack, 0, err);
+        blas_closest(sc, root, 0, r, tmin, h, stack, 0, err, work);
         return h;
     }
     const WRay wr = make_wray(o, d);
@@ -404,6 +410,7 @@ __device__ __forceinline__ Hit closest_hit(const DevScene& sc, const DevFrame& f
     int node = 0;
     while (true) {
         const Node n = load_node(fr.tlas, node);
+        work.x += 1;
         float tl, tr;
         const int m = node_hits(wr, n, tmin, h.t, tl, tr);
         for (int side = 0; side < 2; ++side) {
@@ -414,7 +421,7 @@ __device__ __forceinline__ Hit closest_hit(const DevScene& sc, const DevFrame& f
                     const int inst = ~child + i;
                     int root;
                     const WRay r = object_ray(fr, inst, o, d, root);
-                    blas_closest(sc, root, inst, r, tmin, h, stack, sp, err);
+                    blas_closest(sc, root, inst, r, tmin, h, stack, sp, err, work);
                 }
             }
         }
@@ -442,19 +449,20 @@ __device__ __forceinline__ Hit closest_hit(const DevScene& sc, const DevFrame& f
 }
 
 __device__ __forceinline__ bool occluded(const DevScene& sc, const DevFrame& fr, f3 o, f3 d, float tmin, float tmax,
-                                         int* err) {
+                                         int* err, int2& work) {
     int stack[MCEV_STACK];
     if (fr.n_inst == 0) return false;
     if (fr.tlas_is_leaf) {
         int root;
         const WRay r = object_ray(fr, 0, o, d, root);
-        return blas_any(sc, root, r, tmin, tmax, stack, 0, err);
+        return blas_any(sc, root, r, tmin, tmax, stack, 0, err, work);
     }
     const WRay wr = make_wray(o, d);
     int sp = 0;
     int node = 0;
     while (true) {
         const Node n = load_node(fr.tlas, node);
+        work.x += 1;
         float tl, tr;
         const int m = node_hits(wr, n, tmin, tmax, tl, tr);
         for (int side = 0; side < 2; ++side) {
@@ -465,7 +473,7 @@ __device__ __forceinline__ bool occluded(const DevScene& sc, const DevFrame& fr,
                     const int inst = ~child + i;
                     int root;
                     const WRay r = object_ray(fr, inst, o, d, root);
-                    if (blas_any(sc, root, r, tmin, tmax, stack, sp, err)) return true;
+                    if (blas_any(sc, root, r, tmin, tmax, stack, sp, err, work)) return true;
                 }
             }
         }

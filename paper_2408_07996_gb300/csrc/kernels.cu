@@ -52,21 +52,37 @@ __global__ void __launch_bounds__(256) k_raygen(DevFrame fr, DevParams P, Wave w
     }
 }
 
+// traversal work counters: 64-bit (nodes, tris) pairs after the int32 counters
+enum { WORK_CLOSEST = 0, WORK_SHADOW = 1 };
+__device__ __forceinline__ void add_work(const Wave& w, int which, int2 work) {
+    const unsigned m = __activemask();
+    const int nodes = __reduce_add_sync(m, work.x);
+    const int tris = __reduce_add_sync(m, work.y);
+    if ((threadIdx.x & 31) == (__ffs(m) - 1)) {
+        unsigned long long* c = reinterpret_cast<unsigned long long*>(w.counters + 32);
+        atomicAdd(c + 2 * which, (unsigned long long)nodes);
+        atomicAdd(c + 2 * which + 1, (unsigned long long)tris);
+    }
+}
+
 // ------------------------------------------------------------------ extend
 __global__ void __launch_bounds__(128) k_extend(DevScene sc, DevFrame fr, float t_min, Wave w, int cur, int32_t* err) {
     const int32_t n = *(volatile int32_t*)(w.counters + cur);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         w.counters[1 - cur] = 0;
         w.counters[2] = 0;
+        atomicAdd(reinterpret_cast<unsigned long long*>(w.counters + 32) + 4, (unsigned long long)n);
     }
     int e = 0;
+    int2 work = make_int2(0, 0);
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const float4 o = w.ray_o[cur][i];
         const float4 d = w.ray_d[cur][i];
-        const Hit h = closest_hit(sc, fr, xyz(o), xyz(d), t_min, &e);
+        const Hit h = closest_hit(sc, fr, xyz(o), xyz(d), t_min, &e, work);
         w.hit[i] = make_float4(h.t, __int_as_float(h.inst), __int_as_float(h.tri), 0.0f);
     }
     if (e) atomicOr(err, 1);
+    add_work(w, WORK_CLOSEST, work);
 }
 
 // ------------------------------------------------------------------ shade + NEE + BSDF sampling
@@ -233,17 +249,21 @@ __global__ void __launch_bounds__(128) k_shade(DevScene sc, DevFrame fr, DevPara
 // ------------------------------------------------------------------ shadow rays
 __global__ void __launch_bounds__(128) k_shadow(DevScene sc, DevFrame fr, DevParams P, Wave w, int32_t* err) {
     const int32_t n = *(volatile int32_t*)(w.counters + 2);
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        atomicAdd(reinterpret_cast<unsigned long long*>(w.counters + 32) + 5, (unsigned long long)n);
     int e = 0;
+    int2 work = make_int2(0, 0);
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const float4 o = w.sh_o[i];
         const float4 d = w.sh_d[i];
         const int p = __float_as_int(o.w);
-        if (!occluded(sc, fr, xyz(o), xyz(d), P.t_min, d.w, &e)) {
+        if (!occluded(sc, fr, xyz(o), xyz(d), P.t_min, d.w, &e, work)) {
             w.L[p] += w.sh_c[i];
             if (P.want_sig) w.pflags[p] |= 4u;
         }
     }
     if (e) atomicOr(err, 1);
+    add_work(w, WORK_SHADOW, work);
 }
 
 // ------------------------------------------------------------------ per-pixel statistics + test + requeue + events
