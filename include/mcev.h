@@ -217,6 +217,74 @@ size_t mcev_state_bytes(const mcev_ctx* ctx);
 mcev_status mcev_get_state(mcev_ctx* ctx, void* dev_buf, size_t bytes);
 mcev_status mcev_set_state(mcev_ctx* ctx, const void* dev_buf, size_t bytes);
 
+/* ------------------------------------------------------------------------
+ * Allocation-free detector step.  The paper has no counterpart: this is an
+ * interface of this library for callers that cannot allocate device memory
+ * themselves or let a library do it - for example a renderer embedded in a
+ * host application whose memory pool owns the whole GPU, or a real-time loop
+ * that must not pay for the device synchronisation cudaMalloc/cudaFree imply.
+ * Such a caller brings its own path radiance samples and its own per-pixel
+ * state buffers and runs the same fused statistics / t-test / re-queue /
+ * event kernel that mcev_render_events uses, one batch per call.
+ *
+ * Memory: the kernel's scratch (the re-queue counter, event counters and the
+ * table of critical t values) is a fixed 16,640-byte array in the library's
+ * device image (MCEV_DETECT_STATIC_SCRATCH_BYTES).  Every GPU that loads the
+ * library holds it until the process exits.  The call makes no cudaMalloc,
+ * cudaFree, allocator-hook or framework allocation.
+ *
+ * Set-up: the first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call on
+ * each device before any stream capture begins.
+ *
+ * Sharing: every call on a device uses the same array.  Each call clears
+ * the counters and rewrites the table before its kernel runs, so nothing
+ * carries over between calls, but calls whose GPU work overlaps (different
+ * streams, or several host threads) race on the array and must be
+ * serialised by the caller.  The call synchronises `stream` to return the
+ * number of undecided pixels.
+ * ------------------------------------------------------------------------ */
+#define MCEV_DETECT_STATIC_MAX_TESTS 4096
+#define MCEV_DETECT_STATIC_SCRATCH_BYTES (256 + 4 * MCEV_DETECT_STATIC_MAX_TESTS)
+
+typedef struct {
+    const float* L;          /* device [n_pix][spp_r]: radiance of this batch's paths, pixel-major */
+    const int32_t* pixels;   /* device [n_pix]: pixel ids indexing the per-pixel arrays below */
+    int64_t n_pix;
+    int64_t n_total;         /* length of every per-pixel array; ids outside [0, n_total) are skipped
+                                and reported as MCEV_ERR_ARG */
+    int32_t spp_r;           /* samples per pixel in this batch (>= 1) */
+    int32_t reserved0;       /* must be 0 */
+    int64_t k_base;          /* samples every listed pixel already has this frame (0: first batch) */
+    int32_t* cur_n;          /* device per-pixel running statistics of the frame (in/out) */
+    float* cur_mean;
+    float* cur_m2;
+    int32_t* ref_n;          /* device per-pixel reference statistics (in/out; replaced on an event) */
+    float* ref_mean;
+    float* ref_m2;
+    int8_t* events;          /* device per-pixel event map, written for pixels decided by this call */
+    int32_t* spp_out;        /* device per-pixel sample counts of decided pixels, or NULL */
+    float* mean_out;         /* device per-pixel mean ln(L + eps) of decided pixels, or NULL */
+    int32_t* undecided;      /* device [n_pix] out: pixels that need another batch (any order) */
+    float eps, C, alpha;
+    int32_t spp_min, spp_batch, spp_max;
+    int32_t variant, se_mode;/* as in mcev_params */
+    void* stream;            /* cudaStream_t; NULL = legacy default stream */
+    char* err_msg;           /* host, optional: receives a message when the call fails */
+    size_t err_len;
+} mcev_detect_args;
+
+/* Runs one batch of the detector without allocating: merges each listed
+ * pixel's spp_r samples y = ln(L + eps) into its running statistics, tests
+ * it once it has spp_min samples (a test is done at every sample count
+ * spp_min + r * spp_batch below spp_max), and either lists it in `undecided`
+ * or writes its event, sample count and mean (updating the reference on an
+ * event).  *n_undecided (host) receives the number of pixels listed.
+ * Errors: MCEV_ERR_ARG for null or inconsistent arguments, and for
+ * schedules needing more than MCEV_DETECT_STATIC_MAX_TESTS tests (the table
+ * would not fit the fixed scratch); MCEV_ERR_CUDA for failed CUDA calls. */
+mcev_status mcev_detect_batch_static(const mcev_detect_args* args, int64_t* n_undecided);
+
 #ifdef __cplusplus
 }
 #endif

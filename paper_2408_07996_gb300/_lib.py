@@ -64,6 +64,21 @@ class Stats(C.Structure):
         return d
 
 
+class DetectArgs(C.Structure):
+    _fields_ = [
+        ("L", C.c_void_p), ("pixels", C.c_void_p), ("n_pix", C.c_int64), ("n_total", C.c_int64),
+        ("spp_r", C.c_int32),
+        ("reserved0", C.c_int32), ("k_base", C.c_int64),
+        ("cur_n", C.c_void_p), ("cur_mean", C.c_void_p), ("cur_m2", C.c_void_p),
+        ("ref_n", C.c_void_p), ("ref_mean", C.c_void_p), ("ref_m2", C.c_void_p),
+        ("events", C.c_void_p), ("spp_out", C.c_void_p), ("mean_out", C.c_void_p), ("undecided", C.c_void_p),
+        ("eps", C.c_float), ("C", C.c_float), ("alpha", C.c_float),
+        ("spp_min", C.c_int32), ("spp_batch", C.c_int32), ("spp_max", C.c_int32),
+        ("variant", C.c_int32), ("se_mode", C.c_int32),
+        ("stream", C.c_void_p), ("err_msg", C.c_char_p), ("err_len", C.c_size_t),
+    ]
+
+
 # every symbol include/mcev.h declares, with its ctypes signature
 SIGNATURES = {
     "mcev_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int32, C.c_int32]),
@@ -82,6 +97,7 @@ SIGNATURES = {
     "mcev_state_bytes": (C.c_size_t, [C.c_void_p]),
     "mcev_get_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
     "mcev_set_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
+    "mcev_detect_batch_static": (C.c_int, [C.POINTER(DetectArgs), C.POINTER(C.c_int64)]),
 }
 
 _lib = None

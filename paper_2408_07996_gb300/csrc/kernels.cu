@@ -11,8 +11,12 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
+#include "../../include/mcev.h"
 #include "device.cuh"
 #include "kernels.h"
+#include "tdist.h"
 
 namespace mcev {
 
@@ -281,6 +285,9 @@ __device__ __forceinline__ Moments chan(Moments a, Moments b) {
     return r;
 }
 
+// kChecked: caller-supplied pixel ids and counts are range-checked (the
+// allocation-free entry point); the renderer's own queues use <false>.
+template <bool kChecked>
 __global__ void __launch_bounds__(256) k_stats(Wave w, StatsArgs A, const int32_t* __restrict__ queue, int64_t j0,
                                                int64_t n_pix, int32_t* __restrict__ next_queue) {
     const int lane = threadIdx.x & 31;
@@ -288,6 +295,10 @@ __global__ void __launch_bounds__(256) k_stats(Wave w, StatsArgs A, const int32_
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t j = warp0; j < n_pix; j += nwarps) {
         const int32_t pix = __ldg(queue + j0 + j);
+        if (kChecked && (pix < 0 || (int64_t)pix >= A.n_total)) {
+            if (lane == 0) atomicOr(w.counters + 8, 1);
+            continue;
+        }
         // per-lane Welford over the lane's samples of this batch
         Moments m{0.0f, 0.0f, 0.0f};
         int bad = 0;
@@ -350,9 +361,13 @@ __global__ void __launch_bounds__(256) k_stats(Wave w, StatsArgs A, const int32_
                 const float se2 = A.se_mode == SE_WELCH ? va / (float)na + vb / (float)n : (va + vb) / (float)n;
                 if (se2 == 0.0f) {
                     decided = gap < A.C;
+                } else if (kChecked && n < A.spp_min) {
+                    decided = false;
                 } else {
                     const float t = (gap - A.C) / sqrtf(se2);
-                    const float tc = __ldg(A.tcrit + (n - A.spp_min) / A.spp_batch);
+                    int r = (n - A.spp_min) / A.spp_batch;
+                    if (kChecked) r = min(r, (A.spp_max - A.spp_min + A.spp_batch - 1) / A.spp_batch - 1);
+                    const float tc = __ldg(A.tcrit + r);
                     decided = A.variant == VAR_TWO_TAILED ? (t < tc || t > -tc) : (t < tc);
                 }
             }
@@ -431,7 +446,13 @@ cudaError_t launch_shadow(const DevScene& sc, const DevFrame& fr, const DevParam
 
 cudaError_t launch_stats(const Wave& w, const StatsArgs& A, const int32_t* queue, int64_t j0, int64_t n_pix,
                          int32_t* next_queue, int sms, cudaStream_t st) {
-    k_stats<<<grid_for(n_pix * 32, 256, sms, 8), 256, 0, st>>>(w, A, queue, j0, n_pix, next_queue);
+    k_stats<false><<<grid_for(n_pix * 32, 256, sms, 8), 256, 0, st>>>(w, A, queue, j0, n_pix, next_queue);
+    return cudaGetLastError();
+}
+
+static cudaError_t launch_stats_checked(const Wave& w, const StatsArgs& A, const int32_t* queue, int64_t n_pix,
+                                        int32_t* next_queue, int sms, cudaStream_t st) {
+    k_stats<true><<<grid_for(n_pix * 32, 256, sms, 8), 256, 0, st>>>(w, A, queue, 0, n_pix, next_queue);
     return cudaGetLastError();
 }
 
@@ -447,3 +468,128 @@ cudaError_t launch_iota(int32_t* q, int64_t n, int sms, cudaStream_t st) {
 }
 
 }  // namespace mcev
+
+// ------------------------------------------------------------------ allocation-free detector step
+// Scratch of mcev_detect_batch_static: int32 counters [0, 256) (the layout
+// k_stats expects: [3] re-queue count, [4] non-finite, [5]/[6] events +/-,
+// [7] pixels at the cap) followed by the critical-t table.  It lives in the
+// library image so the call never allocates; host code reaches it only
+// through the address cudaGetSymbolAddress returns for the current device.
+static __device__ __align__(256) unsigned char g_detect_scratch[MCEV_DETECT_STATIC_SCRATCH_BYTES];
+
+namespace {
+
+struct StaticDevice {
+    void* scratch = nullptr;
+    int sms = 0;
+    bool ready = false;
+};
+constexpr int kMaxDevices = 64;
+StaticDevice g_static_dev[kMaxDevices];
+std::mutex g_static_mu;
+
+mcev_status static_fail(const mcev_detect_args* a, mcev_status s, const char* msg) {
+    if (a && a->err_msg && a->err_len > 0) {
+        size_t i = 0;
+        for (; msg[i] && i + 1 < a->err_len; ++i) a->err_msg[i] = msg[i];
+        a->err_msg[i] = 0;
+    }
+    return s;
+}
+
+}  // namespace
+
+extern "C" mcev_status mcev_detect_batch_static(const mcev_detect_args* a, int64_t* n_undecided) {
+    using namespace mcev;
+    if (!a || !n_undecided) return MCEV_ERR_ARG;
+    if (!a->L || !a->pixels || !a->cur_n || !a->cur_mean || !a->cur_m2 || !a->ref_n || !a->ref_mean ||
+        !a->ref_m2 || !a->events || !a->undecided)
+        return static_fail(a, MCEV_ERR_ARG, "mcev_detect_batch_static: a required pointer is NULL");
+    if (a->n_pix < 0 || a->n_total < 1 || a->spp_r < 1 || a->k_base < 0 || a->reserved0 != 0 || a->spp_min < 2 ||
+        a->spp_batch < 1 || a->spp_max < a->spp_min || a->k_base + a->spp_r > a->spp_max ||
+        (a->k_base == 0 && a->spp_r != a->spp_min) || !(a->eps > 0.0f) || !(a->C >= 0.0f) ||
+        !(a->alpha > 0.0f && a->alpha < 1.0f) || a->variant < 0 || a->variant > 3 || a->se_mode < 0 ||
+        a->se_mode > 1 || (int64_t)a->n_pix * a->spp_r > ((int64_t)1 << 40))
+        return static_fail(a, MCEV_ERR_ARG, "mcev_detect_batch_static: inconsistent sizes or settings");
+    const int64_t n_tests = (a->spp_max - a->spp_min + a->spp_batch - 1) / a->spp_batch;
+    if (n_tests > MCEV_DETECT_STATIC_MAX_TESTS)
+        return static_fail(a, MCEV_ERR_ARG,
+                           "mcev_detect_batch_static: the schedule needs more than 4096 t-tests; the fixed "
+                           "scratch holds 4096 critical values (raise spp_batch or lower spp_max)");
+    *n_undecided = 0;
+    if (a->n_pix == 0) return MCEV_OK;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        cudaGetLastError();
+        return static_fail(a, MCEV_ERR_CUDA, "mcev_detect_batch_static: no usable current CUDA device");
+    }
+    StaticDevice sd;
+    {
+        std::lock_guard<std::mutex> lock(g_static_mu);
+        StaticDevice& s = g_static_dev[dev];
+        if (!s.ready) {
+            void* p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_detect_scratch) != cudaSuccess || !p) {
+                cudaGetLastError();
+                return static_fail(a, MCEV_ERR_CUDA, "mcev_detect_batch_static: cudaGetSymbolAddress failed");
+            }
+            int sms = 0;
+            if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+                cudaGetLastError();
+                return static_fail(a, MCEV_ERR_CUDA, "mcev_detect_batch_static: device query failed");
+            }
+            s.scratch = p;
+            s.sms = sms;
+            s.ready = true;
+        }
+        sd = s;
+    }
+    cudaStream_t st = (cudaStream_t)a->stream;
+    int32_t* counters = (int32_t*)sd.scratch;
+    float* tcrit = (float*)((unsigned char*)sd.scratch + 256);
+    float tab[MCEV_DETECT_STATIC_MAX_TESTS];
+    int nt = 0;
+    if (a->variant == VAR_ONE_TAILED || a->variant == VAR_TWO_TAILED) {
+        const double p = a->variant == VAR_TWO_TAILED ? 0.5 * (double)a->alpha : (double)a->alpha;
+        for (int n = a->spp_min; n < a->spp_max; n += a->spp_batch) tab[nt++] = (float)t_quantile_int(p, n - 1);
+    }
+    if (cudaMemsetAsync(counters, 0, 256, st) != cudaSuccess ||
+        (nt > 0 && cudaMemcpyAsync(tcrit, tab, sizeof(float) * nt, cudaMemcpyHostToDevice, st) != cudaSuccess)) {
+        cudaGetLastError();
+        return static_fail(a, MCEV_ERR_CUDA, "mcev_detect_batch_static: scratch initialisation failed");
+    }
+    Wave w{};
+    w.L = const_cast<float*>(a->L);
+    w.counters = counters;
+    StatsArgs A{};
+    A.cur = PixStats{a->cur_n, a->cur_mean, a->cur_m2};
+    A.ref = PixStats{a->ref_n, a->ref_mean, a->ref_m2};
+    A.tcrit = tcrit;
+    A.events = a->events;
+    A.spp_out = a->spp_out;
+    A.mean_out = a->mean_out;
+    A.eps = a->eps;
+    A.C = a->C;
+    A.spp_r = a->spp_r;
+    A.k_base = a->k_base;
+    A.spp_min = a->spp_min;
+    A.spp_batch = a->spp_batch;
+    A.spp_max = a->spp_max;
+    A.mode = MODE_DETECT;
+    A.variant = a->variant;
+    A.se_mode = a->se_mode;
+    A.n_total = a->n_total;
+    if (launch_stats_checked(w, A, a->pixels, a->n_pix, a->undecided, sd.sms, st) != cudaSuccess)
+        return static_fail(a, MCEV_ERR_CUDA, "mcev_detect_batch_static: kernel launch failed");
+    int32_t c[16];
+    if (cudaMemcpyAsync(c, counters, sizeof c, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+        cudaGetLastError();
+        return static_fail(a, MCEV_ERR_CUDA, "mcev_detect_batch_static: kernel or copy failed");
+    }
+    *n_undecided = c[3];
+    if (c[8])
+        return static_fail(a, MCEV_ERR_ARG,
+                           "mcev_detect_batch_static: a pixel id was outside [0, n_total); those pixels were skipped");
+    return MCEV_OK;
+}

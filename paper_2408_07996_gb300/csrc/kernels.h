@@ -22,6 +22,7 @@ struct StatsArgs {
     int64_t k_base;       // samples taken before this batch
     int32_t spp_min, spp_batch, spp_max;
     int32_t mode, variant, se_mode;
+    int64_t n_total;      // per-pixel array length, checked only by the allocation-free entry point
 };
 
 cudaError_t launch_raygen(const DevFrame& fr, const DevParams& P, const Wave& w, const int32_t* queue, int64_t j0,
