@@ -82,6 +82,11 @@ struct mcev_ctx {
     bool env_ok = false;
     int sah_bins = 32, max_leaf = 4;
     int bvh_depth = 0;
+    std::vector<char> inst_static;          // keyframes never change
+    std::vector<float> static_vtx;          // world-space triangles of static instances
+    bool has_static = false;
+    int static_root = -1;
+    float static_lo[3], static_hi[3];
 
     // device scene
     DevBuf d_nodes, d_tris, d_mats, d_env, d_marg, d_cond, d_tpdf;
@@ -243,57 +248,128 @@ uint32_t frame_key(double t) {
 }
 
 // ---------------------------------------------------------------- scene build
+// One BVH per mesh that a moving instance uses (object space, shared by its
+// instances) and one BVH over the world-space triangles of every instance
+// whose keyframes never change (merged, so rays skip the instance level).
+struct TriSrc {
+    const float* v;  // 9 floats
+    int32_t prim, mat, inst;
+};
+
+mcev_status build_one(mcev_ctx* ctx, const std::vector<TriSrc>& src, std::vector<Node>& nodes,
+                      std::vector<float4>& tris, int& root, float lo_out[3], float hi_out[3], int& depth) {
+    const int n = (int)src.size();
+    std::vector<float> lo(3 * (size_t)n), hi(3 * (size_t)n), ce(3 * (size_t)n);
+    for (int i = 0; i < n; ++i) {
+        const float* v = src[i].v;
+        for (int a = 0; a < 3; ++a) {
+            lo[3 * i + a] = std::min(v[a], std::min(v[3 + a], v[6 + a]));
+            hi[3 * i + a] = std::max(v[a], std::max(v[3 + a], v[6 + a]));
+            ce[3 * i + a] = (float)(((double)v[a] + v[3 + a] + v[6 + a]) / 3.0);
+        }
+    }
+    BuiltBvh b = build_bvh(lo.data(), hi.data(), ce.data(), n, ctx->sah_bins, ctx->max_leaf);
+    depth = std::max(depth, b.depth);
+    const int node_off = (int)nodes.size();
+    const int64_t tri_off = (int64_t)tris.size() / 3;
+    root = node_off;
+    for (Node nd : b.nodes) {
+        if (nd.d.x >= 0) nd.d.x += node_off;
+        else nd.d.x = ~(int)(tri_off + ~nd.d.x);
+        if (nd.d.y >= 0) nd.d.y += node_off;
+        else nd.d.y = ~(int)(tri_off + ~nd.d.y);
+        nodes.push_back(nd);
+    }
+    for (int k = 0; k < 3; ++k) {
+        lo_out[k] = std::numeric_limits<float>::max();
+        hi_out[k] = -std::numeric_limits<float>::max();
+    }
+    for (int i = 0; i < n; ++i) {
+        const TriSrc& s = src[b.order[i]];
+        const float* v = s.v;
+        float4 t0, t1, t2;
+        t0.x = v[0]; t0.y = v[1]; t0.z = v[2];
+        std::memcpy(&t0.w, &s.prim, 4);
+        t1.x = v[3]; t1.y = v[4]; t1.z = v[5];
+        std::memcpy(&t1.w, &s.mat, 4);
+        t2.x = v[6]; t2.y = v[7]; t2.z = v[8];
+        std::memcpy(&t2.w, &s.inst, 4);
+        tris.push_back(t0);
+        tris.push_back(t1);
+        tris.push_back(t2);
+        for (int a = 0; a < 3; ++a) {
+            lo_out[a] = std::min(lo_out[a], std::min(v[a], std::min(v[3 + a], v[6 + a])));
+            hi_out[a] = std::max(hi_out[a], std::max(v[a], std::max(v[3 + a], v[6 + a])));
+        }
+    }
+    return MCEV_OK;
+}
+
 mcev_status build_blas(mcev_ctx* ctx) {
     std::vector<Node> nodes;
     std::vector<float4> tris;
     tris.reserve(ctx->vtx.size() / 3);
     int depth = 0;
-    for (auto& m : ctx->meshes) {
-        const int n = (int)m.n_tri;
-        std::vector<float> lo(3 * (size_t)n), hi(3 * (size_t)n), ce(3 * (size_t)n);
-        for (int i = 0; i < n; ++i) {
-            const float* v = &ctx->vtx[9 * (size_t)(m.first_tri + i)];
-            for (int a = 0; a < 3; ++a) {
-                lo[3 * i + a] = std::min(v[a], std::min(v[3 + a], v[6 + a]));
-                hi[3 * i + a] = std::max(v[a], std::max(v[3 + a], v[6 + a]));
-                ce[3 * i + a] = (float)(((double)v[a] + v[3 + a] + v[6 + a]) / 3.0);
-            }
+    const int ni = ctx->n_inst, nk = ctx->n_keys;
+    ctx->inst_static.assign(ni, 1);
+    for (int i = 0; i < ni; ++i)
+        for (int k = 1; k < nk && ctx->inst_static[i]; ++k)
+            if (std::memcmp(&ctx->key_xf[12 * ((size_t)k * ni + i)], &ctx->key_xf[12 * (size_t)i],
+                            12 * sizeof(double)) != 0)
+                ctx->inst_static[i] = 0;
+    std::vector<char> mesh_dynamic(ctx->meshes.size(), 0);
+    for (int i = 0; i < ni; ++i)
+        if (!ctx->inst_static[i]) mesh_dynamic[ctx->inst_mesh[i]] = 1;
+    for (size_t mi = 0; mi < ctx->meshes.size(); ++mi) {
+        MeshInfo& m = ctx->meshes[mi];
+        m.root = -1;
+        if (!mesh_dynamic[mi]) continue;
+        std::vector<TriSrc> src((size_t)m.n_tri);
+        for (int64_t t = 0; t < m.n_tri; ++t) {
+            const int64_t prim = m.first_tri + t;
+            src[t] = TriSrc{&ctx->vtx[9 * (size_t)prim], (int32_t)prim, ctx->tri_mat[prim], -1};
         }
-        BuiltBvh b = build_bvh(lo.data(), hi.data(), ce.data(), n, ctx->sah_bins, ctx->max_leaf);
-        depth = std::max(depth, b.depth);
-        const int node_off = (int)nodes.size();
-        m.tri_offset = (int64_t)tris.size() / 3;
-        m.root = node_off;
-        for (Node nd : b.nodes) {
-            if (nd.d.x >= 0) nd.d.x += node_off;
-            else nd.d.x = ~(int)(m.tri_offset + ~nd.d.x);
-            if (nd.d.y >= 0) nd.d.y += node_off;
-            else nd.d.y = ~(int)(m.tri_offset + ~nd.d.y);
-            nodes.push_back(nd);
-        }
-        for (int k = 0; k < 3; ++k) {
-            m.lo[k] = std::numeric_limits<float>::max();
-            m.hi[k] = -std::numeric_limits<float>::max();
-        }
-        for (int i = 0; i < n; ++i) {
-            const int64_t prim = m.first_tri + b.order[i];
+        ST(build_one(ctx, src, nodes, tris, m.root, m.lo, m.hi, depth));
+    }
+    // merged static geometry in world space (keyframe 0 transform, FP64 -> FP32)
+    ctx->static_vtx.clear();
+    std::vector<TriSrc> ssrc;
+    size_t n_static_tris = 0;
+    for (int i = 0; i < ni; ++i)
+        if (ctx->inst_static[i]) n_static_tris += (size_t)ctx->meshes[ctx->inst_mesh[i]].n_tri;
+    ctx->static_vtx.resize(9 * n_static_tris);
+    ssrc.reserve(n_static_tris);
+    size_t w = 0;
+    for (int i = 0; i < ni; ++i) {
+        if (!ctx->inst_static[i]) continue;
+        const double* M = &ctx->key_xf[12 * (size_t)i];
+        const MeshInfo& m = ctx->meshes[ctx->inst_mesh[i]];
+        for (int64_t t = 0; t < m.n_tri; ++t) {
+            const int64_t prim = m.first_tri + t;
             const float* v = &ctx->vtx[9 * (size_t)prim];
-            float4 t0, t1, t2;
-            t0.x = v[0]; t0.y = v[1]; t0.z = v[2];
-            int pi = (int)prim, mi = ctx->tri_mat[prim];
-            std::memcpy(&t0.w, &pi, 4);
-            t1.x = v[3]; t1.y = v[4]; t1.z = v[5];
-            std::memcpy(&t1.w, &mi, 4);
-            t2.x = v[6]; t2.y = v[7]; t2.z = v[8]; t2.w = 0.0f;
-            tris.push_back(t0);
-            tris.push_back(t1);
-            tris.push_back(t2);
-            for (int a = 0; a < 3; ++a) {
-                m.lo[a] = std::min(m.lo[a], std::min(v[a], std::min(v[3 + a], v[6 + a])));
-                m.hi[a] = std::max(m.hi[a], std::max(v[a], std::max(v[3 + a], v[6 + a])));
+            float* o = &ctx->static_vtx[9 * w];
+            for (int c = 0; c < 3; ++c) {
+                const double p[3] = {v[3 * c], v[3 * c + 1], v[3 * c + 2]};
+                double q[3];
+                xf_point(M, p, q);
+                o[3 * c] = (float)q[0];
+                o[3 * c + 1] = (float)q[1];
+                o[3 * c + 2] = (float)q[2];
             }
+            const int32_t mat = ctx->inst_mat[i] >= 0 ? ctx->inst_mat[i] : ctx->tri_mat[prim];
+            ssrc.push_back(TriSrc{o, (int32_t)prim, mat, i});
+            ++w;
         }
     }
+    ctx->static_root = -1;
+    ctx->has_static = n_static_tris > 0;
+    if (ctx->has_static) ST(build_one(ctx, ssrc, nodes, tris, ctx->static_root, ctx->static_lo, ctx->static_hi, depth));
+    if (nodes.empty()) {
+        Node none;
+        std::memset(&none, 0, sizeof none);
+        nodes.push_back(none);
+    }
+    if (tris.empty()) tris.push_back(make_float4(0, 0, 0, 0));
     if (depth + 16 > MCEV_STACK_HOST)
         return fail(ctx, MCEV_ERR_ARG, "BVH depth %d exceeds the traversal stack", depth);
     ctx->bvh_depth = depth;
@@ -363,54 +439,70 @@ mcev_status frame_setup(mcev_ctx* ctx, double t, int slot) {
     const int k1 = nk > 1 ? k + 1 : k;
     auto lerp = [f](double a, double b) { return (1.0 - f) * a + f * b; };
     std::vector<double> M((size_t)ni * 12), Mi((size_t)ni * 12);
-    std::vector<float> blo(3 * (size_t)ni), bhi(3 * (size_t)ni), bce(3 * (size_t)ni);
-    std::vector<float4> inst((size_t)ni * 7);
     for (int i = 0; i < ni; ++i) {
         const double* A = &ctx->key_xf[12 * ((size_t)k * ni + i)];
         const double* B = &ctx->key_xf[12 * ((size_t)k1 * ni + i)];
         double* m = &M[12 * (size_t)i];
         for (int e = 0; e < 12; ++e) m[e] = lerp(A[e], B[e]);
-        double* mi = &Mi[12 * (size_t)i];
-        affine_inverse(m, mi);
-        const MeshInfo& mesh = ctx->meshes[ctx->inst_mesh[i]];
+        affine_inverse(m, &Mi[12 * (size_t)i]);
+    }
+    // instance records: every moving instance, then the merged static geometry
+    std::vector<int> rec_inst;
+    for (int i = 0; i < ni; ++i)
+        if (!ctx->inst_static[i]) rec_inst.push_back(i);
+    if (ctx->has_static) rec_inst.push_back(-1);
+    const int nr = (int)rec_inst.size();
+    std::vector<float> blo(3 * (size_t)nr), bhi(3 * (size_t)nr), bce(3 * (size_t)nr);
+    std::vector<float4> inst((size_t)nr * 7);
+    static const double ident[12] = {1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0};
+    for (int r = 0; r < nr; ++r) {
+        const int i = rec_inst[r];
+        const double* m = i >= 0 ? &M[12 * (size_t)i] : ident;
+        const double* mi = i >= 0 ? &Mi[12 * (size_t)i] : ident;
+        const float* olo = i >= 0 ? ctx->meshes[ctx->inst_mesh[i]].lo : ctx->static_lo;
+        const float* ohi = i >= 0 ? ctx->meshes[ctx->inst_mesh[i]].hi : ctx->static_hi;
+        const bool empty = i >= 0 ? ctx->meshes[ctx->inst_mesh[i]].n_tri == 0 : false;
         float lo[3] = {std::numeric_limits<float>::max(), std::numeric_limits<float>::max(),
                        std::numeric_limits<float>::max()};
         float hi[3] = {-lo[0], -lo[1], -lo[2]};
-        if (mesh.n_tri > 0) {
+        if (!empty) {
             for (int c = 0; c < 8; ++c) {
-                const double q[3] = {(c & 1) ? mesh.hi[0] : mesh.lo[0], (c & 2) ? mesh.hi[1] : mesh.lo[1],
-                                     (c & 4) ? mesh.hi[2] : mesh.lo[2]};
-                double w[3];
-                xf_point(m, q, w);
-                for (int a = 0; a < 3; ++a) {
+                const double q[3] = {(c & 1) ? ohi[0] : olo[0], (c & 2) ? ohi[1] : olo[1], (c & 4) ? ohi[2] : olo[2]};
+                double wv[3];
+                xf_point(m, q, wv);
+                for (int a2 = 0; a2 < 3; ++a2) {
                     // round outwards so the FP32 box contains the FP64 corners
-                    lo[a] = std::min(lo[a], std::nextafter((float)w[a], -INFINITY));
-                    hi[a] = std::max(hi[a], std::nextafter((float)w[a], INFINITY));
+                    lo[a2] = std::min(lo[a2], std::nextafter((float)wv[a2], -INFINITY));
+                    hi[a2] = std::max(hi[a2], std::nextafter((float)wv[a2], INFINITY));
                 }
             }
         } else {
-            for (int a = 0; a < 3; ++a) lo[a] = hi[a] = 1e30f;
+            for (int a2 = 0; a2 < 3; ++a2) lo[a2] = hi[a2] = 1e30f;
         }
-        for (int a = 0; a < 3; ++a) {
-            blo[3 * i + a] = lo[a];
-            bhi[3 * i + a] = hi[a];
-            bce[3 * i + a] = 0.5f * (lo[a] + hi[a]);
+        for (int a2 = 0; a2 < 3; ++a2) {
+            blo[3 * r + a2] = lo[a2];
+            bhi[3 * r + a2] = hi[a2];
+            bce[3 * r + a2] = 0.5f * (lo[a2] + hi[a2]);
         }
-        for (int r = 0; r < 3; ++r) {
-            inst[7 * i + r] = make_float4((float)m[4 * r], (float)m[4 * r + 1], (float)m[4 * r + 2], (float)m[4 * r + 3]);
-            inst[7 * i + 3 + r] =
-                make_float4((float)mi[4 * r], (float)mi[4 * r + 1], (float)mi[4 * r + 2], (float)mi[4 * r + 3]);
+        for (int row = 0; row < 3; ++row) {
+            inst[7 * r + row] = make_float4((float)m[4 * row], (float)m[4 * row + 1], (float)m[4 * row + 2],
+                                            (float)m[4 * row + 3]);
+            inst[7 * r + 3 + row] = make_float4((float)mi[4 * row], (float)mi[4 * row + 1], (float)mi[4 * row + 2],
+                                                (float)mi[4 * row + 3]);
         }
-        int root = mesh.root, ovr = ctx->inst_mat[i];
+        int root = i >= 0 ? ctx->meshes[ctx->inst_mesh[i]].root : ctx->static_root;
+        int ovr = i >= 0 ? ctx->inst_mat[i] : -1;
+        int oid = i;
         float4 tail = make_float4(0, 0, 0, 0);
         std::memcpy(&tail.x, &root, 4);
         std::memcpy(&tail.y, &ovr, 4);
-        inst[7 * i + 6] = tail;
+        std::memcpy(&tail.z, &oid, 4);
+        inst[7 * r + 6] = tail;
     }
-    // TLAS over instance boxes, one instance per leaf; leaf ref = ~instance id
+    // TLAS over instance records, one record per leaf; leaf ref = ~record
     std::vector<Node> tlas;
-    if (ni > 1) {
-        BuiltBvh b = build_bvh(blo.data(), bhi.data(), bce.data(), ni, 16, 1);
+    if (nr > 1) {
+        BuiltBvh b = build_bvh(blo.data(), bhi.data(), bce.data(), nr, 16, 1);
         tlas = b.nodes;
         for (Node& nd : tlas) {
             if (nd.d.x < 0 && nd.d.z > 0) nd.d.x = ~b.order[~nd.d.x];
@@ -463,9 +555,9 @@ mcev_status frame_setup(mcev_ctx* ctx, double t, int slot) {
     d.tlas = (const Node*)base;
     d.inst = (const float4*)(base + al(nb_t));
     d.lights = (const float4*)(base + al(nb_t) + al(nb_i));
-    d.n_inst = ni;
+    d.n_inst = nr;
     d.n_lights = (int32_t)ctx->emitters.size();
-    d.tlas_is_leaf = ni <= 1 ? 1 : 0;
+    d.tlas_is_leaf = nr <= 1 ? 1 : 0;
     // camera (FP64 then rounded)
     double eye[3], tgt[3], up[3];
     for (int a = 0; a < 3; ++a) {
@@ -509,7 +601,7 @@ mcev_status frame_setup(mcev_ctx* ctx, double t, int slot) {
 
 // ---------------------------------------------------------------- buffers
 mcev_status ensure_wave(mcev_ctx* ctx) {
-    const int64_t cap = ctx->params.wavefront > 0 ? ctx->params.wavefront : ((int64_t)1 << 23);
+    const int64_t cap = ctx->params.wavefront > 0 ? ctx->params.wavefront : ((int64_t)1 << 25);
     if (ctx->d_wave.ptr && ctx->wave.cap == cap) return MCEV_OK;
     const size_t per = 4 * 3 + 4 * 2 + 8 + 16 * 2 * 2 + 16 + 16 * 2 + 4;
     ST(dev_alloc(ctx, ctx->d_wave, (size_t)cap * per + 64 * 256));

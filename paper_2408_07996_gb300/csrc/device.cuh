@@ -271,9 +271,10 @@ __device__ __forceinline__ Node load_node(const Node* nodes, int i) {
 
 struct Hit {
     float t;
-    int inst;
+    int inst;   // uploaded instance id (ties, signature)
     int tri;    // leaf-order triangle index
     int prim;   // uploaded triangle id (ties)
+    int rec;    // instance record of the frame (transform)
 };
 
 __device__ __forceinline__ bool better_hit(float t, int inst, int prim, const Hit& h) {
@@ -284,7 +285,9 @@ __device__ __forceinline__ bool better_hit(float t, int inst, int prim, const Hi
 }
 
 // BLAS closest hit of an object-space ray; updates h
-__device__ __forceinline__ void blas_closest(const DevScene& sc, int root, int inst, const WRay& r,
+// rec: instance record; inst: its uploaded instance id, or -1 for the merged
+// static geometry whose triangles carry their own instance id (v2.w)
+__device__ __forceinline__ void blas_closest(const DevScene& sc, int root, int rec, int inst, const WRay& r,
                                              float tmin, Hit& h, int* stack, int base, int* err, int2& work) {
     int sp = base;
     int node = root;
@@ -302,8 +305,9 @@ __device__ __forceinline__ void blas_closest(const DevScene& sc, int root, int i
                 const float4* tp = sc.tris + 3 * (first + i);
                 const float4 p0 = __ldg(tp), p1 = __ldg(tp + 1), p2 = __ldg(tp + 2);
                 const float t = tri_hit(r, p0, p1, p2, tmin, h.t);
-                if (t >= 0.0f && better_hit(t, inst, __float_as_int(p0.w), h)) {
-                    h.t = t; h.inst = inst; h.tri = first + i; h.prim = __float_as_int(p0.w);
+                const int oi = inst >= 0 ? inst : __float_as_int(p2.w);
+                if (t >= 0.0f && better_hit(t, oi, __float_as_int(p0.w), h)) {
+                    h.t = t; h.inst = oi; h.tri = first + i; h.prim = __float_as_int(p0.w); h.rec = rec;
                 }
             }
         }
@@ -314,8 +318,9 @@ __device__ __forceinline__ void blas_closest(const DevScene& sc, int root, int i
                 const float4* tp = sc.tris + 3 * (first + i);
                 const float4 p0 = __ldg(tp), p1 = __ldg(tp + 1), p2 = __ldg(tp + 2);
                 const float t = tri_hit(r, p0, p1, p2, tmin, h.t);
-                if (t >= 0.0f && better_hit(t, inst, __float_as_int(p0.w), h)) {
-                    h.t = t; h.inst = inst; h.tri = first + i; h.prim = __float_as_int(p0.w);
+                const int oi = inst >= 0 ? inst : __float_as_int(p2.w);
+                if (t >= 0.0f && better_hit(t, oi, __float_as_int(p0.w), h)) {
+                    h.t = t; h.inst = oi; h.tri = first + i; h.prim = __float_as_int(p0.w); h.rec = rec;
                 }
             }
         }
@@ -381,11 +386,13 @@ __device__ __forceinline__ bool blas_any(const DevScene& sc, int root, const WRa
     }
 }
 
-// instance record: rows M0..M2, Minv0..Minv2, (root, override, 0, 0)
-__device__ __forceinline__ WRay object_ray(const DevFrame& fr, int inst, f3 o, f3 d, int& root) {
-    const float4* ip = fr.inst + 7 * inst;
+// instance record: rows M0..M2, Minv0..Minv2, (root, override, instance id, 0)
+__device__ __forceinline__ WRay object_ray(const DevFrame& fr, int rec, f3 o, f3 d, int& root, int& inst) {
+    const float4* ip = fr.inst + 7 * rec;
     const float4 i0 = __ldg(ip + 3), i1 = __ldg(ip + 4), i2 = __ldg(ip + 5);
-    root = __float_as_int(__ldg(ip + 6).x);
+    const float4 tail = __ldg(ip + 6);
+    root = __float_as_int(tail.x);
+    inst = __float_as_int(tail.z);
     return make_wray(xf_point(i0, i1, i2, o), xf_vec(i0, i1, i2, d));
 }
 
@@ -397,12 +404,13 @@ __device__ __forceinline__ Hit closest_hit(const DevScene& sc, const DevFrame& f
     h.inst = -1;
     h.tri = -1;
     h.prim = -1;
+    h.rec = -1;
     int stack[MCEV_STACK];
     if (fr.n_inst == 0) return h;
     if (fr.tlas_is_leaf) {
-        int root;
-        const WRay r = object_ray(fr, 0, o, d, root);
-        blas_closest(sc, root, 0, r, tmin, h, stack, 0, err, work);
+        int root, oi;
+        const WRay r = object_ray(fr, 0, o, d, root, oi);
+        blas_closest(sc, root, 0, oi, r, tmin, h, stack, 0, err, work);
         return h;
     }
     const WRay wr = make_wray(o, d);
@@ -418,10 +426,10 @@ __device__ __forceinline__ Hit closest_hit(const DevScene& sc, const DevFrame& f
             const int cnt = side ? n.d.w : n.d.z;
             if ((m & (1 << side)) && child < 0) {
                 for (int i = 0; i < cnt; ++i) {
-                    const int inst = ~child + i;
-                    int root;
-                    const WRay r = object_ray(fr, inst, o, d, root);
-                    blas_closest(sc, root, inst, r, tmin, h, stack, sp, err, work);
+                    const int rec = ~child + i;
+                    int root, oi;
+                    const WRay r = object_ray(fr, rec, o, d, root, oi);
+                    blas_closest(sc, root, rec, oi, r, tmin, h, stack, sp, err, work);
                 }
             }
         }
@@ -453,8 +461,8 @@ __device__ __forceinline__ bool occluded(const DevScene& sc, const DevFrame& fr,
     int stack[MCEV_STACK];
     if (fr.n_inst == 0) return false;
     if (fr.tlas_is_leaf) {
-        int root;
-        const WRay r = object_ray(fr, 0, o, d, root);
+        int root, oi;
+        const WRay r = object_ray(fr, 0, o, d, root, oi);
         return blas_any(sc, root, r, tmin, tmax, stack, 0, err, work);
     }
     const WRay wr = make_wray(o, d);
@@ -470,9 +478,9 @@ __device__ __forceinline__ bool occluded(const DevScene& sc, const DevFrame& fr,
             const int cnt = side ? n.d.w : n.d.z;
             if ((m & (1 << side)) && child < 0) {
                 for (int i = 0; i < cnt; ++i) {
-                    const int inst = ~child + i;
-                    int root;
-                    const WRay r = object_ray(fr, inst, o, d, root);
+                    const int rec = ~child + i;
+                    int root, oi;
+                    const WRay r = object_ray(fr, rec, o, d, root, oi);
                     if (blas_any(sc, root, r, tmin, tmax, stack, sp, err, work)) return true;
                 }
             }

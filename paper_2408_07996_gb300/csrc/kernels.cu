@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(128) k_extend(DevScene sc, DevFrame fr, float 
         const float4 o = w.ray_o[cur][i];
         const float4 d = w.ray_d[cur][i];
         const Hit h = closest_hit(sc, fr, xyz(o), xyz(d), t_min, &e, work);
-        w.hit[i] = make_float4(h.t, __int_as_float(h.inst), __int_as_float(h.tri), 0.0f);
+        w.hit[i] = make_float4(h.t, __int_as_float(h.inst), __int_as_float(h.tri), __int_as_float(h.rec));
     }
     if (e) atomicOr(err, 1);
     add_work(w, WORK_CLOSEST, work);
@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(128) k_shade(DevScene sc, DevFrame fr, DevPara
             const int tri = __float_as_int(hv.z);
             const float4* tp = sc.tris + 3 * tri;
             const float4 q0 = __ldg(tp), q1 = __ldg(tp + 1), q2 = __ldg(tp + 2);
-            const float4* ip = fr.inst + 7 * inst;
+            const float4* ip = fr.inst + 7 * __float_as_int(hv.w);
             const float4 m0 = __ldg(ip), m1 = __ldg(ip + 1), m2 = __ldg(ip + 2);
             const float4 i0 = __ldg(ip + 3), i1 = __ldg(ip + 4), i2 = __ldg(ip + 5);
             const int ovr = __float_as_int(__ldg(ip + 6).y);

@@ -8,10 +8,13 @@
 //   where a child >= 0 is an inner node and a child < 0 is a leaf holding
 //   triangles [~child, ~child + count) of the triangle array (TLAS leaves
 //   hold instance ids instead of triangles).
-//   Triangle (48 B): v0.xyz|prim, v1.xyz|material, v2.xyz|0 (object space,
-//   BVH leaf order; prim = index in the uploaded triangle list).
-//   Instance (112 B): M rows 0..2, Minv rows 0..2 (3x4 each, float4), then
-//   (blas root node, material override, 0, 0).
+//   Triangle (48 B): v0.xyz|prim, v1.xyz|material, v2.xyz|instance, in BVH
+//   leaf order; prim = index in the uploaded triangle list.  Triangles of a
+//   mesh used by moving instances are in object space with instance = -1;
+//   instances that never move are merged at upload into one world-space
+//   BVH whose triangles carry their instance id and resolved material.
+//   Instance record (112 B): M rows 0..2, Minv rows 0..2 (3x4 each, float4),
+//   then (blas root node, material override, instance id or -1, 0).
 //   Light (64 B): v0.xyz|Le, v1.xyz|area, v2.xyz|0, n.xyz|0 (world space).
 #pragma once
 #include <cuda_runtime.h>
