@@ -370,8 +370,9 @@ mcev_status build_blas(mcev_ctx* ctx) {
         nodes.push_back(none);
     }
     if (tris.empty()) tris.push_back(make_float4(0, 0, 0, 0));
-    if (depth + 16 > MCEV_STACK_HOST)
-        return fail(ctx, MCEV_ERR_ARG, "BVH depth %d exceeds the traversal stack", depth);
+    // a traversal pushes at most one entry per inner-node level
+    if (depth > MCEV_STACK_HOST)
+        return fail(ctx, MCEV_ERR_ARG, "BVH depth %d exceeds the traversal stack (%d)", depth, MCEV_STACK_HOST);
     ctx->bvh_depth = depth;
     ST(upload(ctx, ctx->d_nodes, nodes.data(), nodes.size() * sizeof(Node)));
     ST(upload(ctx, ctx->d_tris, tris.data(), tris.size() * sizeof(float4)));
@@ -508,8 +509,8 @@ mcev_status frame_setup(mcev_ctx* ctx, double t, int slot) {
             if (nd.d.x < 0 && nd.d.z > 0) nd.d.x = ~b.order[~nd.d.x];
             if (nd.d.y < 0 && nd.d.w > 0) nd.d.y = ~b.order[~nd.d.y];
         }
-        if (b.depth + ctx->bvh_depth + 8 > MCEV_STACK_HOST)
-            return fail(ctx, MCEV_ERR_ARG, "TLAS + BLAS depth exceeds the traversal stack");
+        if (b.depth + ctx->bvh_depth > MCEV_STACK_HOST)
+            return fail(ctx, MCEV_ERR_ARG, "TLAS + BLAS depth exceeds the traversal stack (%d)", MCEV_STACK_HOST);
     }
     // emitters in world space
     std::vector<float4> lights(ctx->emitters.size() * 4);

@@ -20,6 +20,17 @@ namespace mcev {
 
 #define MCEV_PI 3.14159265358979323846f
 #define MCEV_STACK MCEV_STACK_HOST
+// traversal kernels run 128-thread blocks; the shared stack interleaves threads
+#define MCEV_TRAV_BLOCK 128
+#if MCEV_SMEM_STACK
+#define SIDX(i) ((i) * MCEV_TRAV_BLOCK)
+#define MCEV_DECLARE_STACK(name)                               \
+    __shared__ int name##_smem[MCEV_STACK * MCEV_TRAV_BLOCK];  \
+    int* name = name##_smem + threadIdx.x
+#else
+#define SIDX(i) (i)
+#define MCEV_DECLARE_STACK(name) int name[MCEV_STACK]
+#endif
 
 // ------------------------------------------------------------------ math
 struct f3 {
@@ -329,7 +340,7 @@ __device__ __forceinline__ void blas_closest(const DevScene& sc, int root, int r
         if (gl && gr) {
             const int nearc = tl <= tr ? n.d.x : n.d.y;
             const int farc = tl <= tr ? n.d.y : n.d.x;
-            if (sp < MCEV_STACK) stack[sp++] = farc;
+            if (sp < MCEV_STACK) stack[SIDX(sp++)] = farc;
             else *err = 1;
             next = nearc;
         } else if (gl) {
@@ -339,7 +350,7 @@ __device__ __forceinline__ void blas_closest(const DevScene& sc, int root, int r
         }
         if (next == -0x7fffffff) {
             if (sp == base) break;
-            next = stack[--sp];
+            next = stack[SIDX(--sp)];
         }
         node = next;
     }
@@ -370,7 +381,7 @@ __device__ __forceinline__ bool blas_any(const DevScene& sc, int root, const WRa
         const bool gr = (m & 2) && n.d.y >= 0;
         int next = -0x7fffffff;
         if (gl && gr) {
-            if (sp < MCEV_STACK) stack[sp++] = n.d.y;
+            if (sp < MCEV_STACK) stack[SIDX(sp++)] = n.d.y;
             else *err = 1;
             next = n.d.x;
         } else if (gl) {
@@ -380,7 +391,7 @@ __device__ __forceinline__ bool blas_any(const DevScene& sc, int root, const WRa
         }
         if (next == -0x7fffffff) {
             if (sp == base) return false;
-            next = stack[--sp];
+            next = stack[SIDX(--sp)];
         }
         node = next;
     }
@@ -405,7 +416,7 @@ __device__ __forceinline__ Hit closest_hit(const DevScene& sc, const DevFrame& f
     h.tri = -1;
     h.prim = -1;
     h.rec = -1;
-    int stack[MCEV_STACK];
+    MCEV_DECLARE_STACK(stack);
     if (fr.n_inst == 0) return h;
     if (fr.tlas_is_leaf) {
         int root, oi;
@@ -439,7 +450,7 @@ __device__ __forceinline__ Hit closest_hit(const DevScene& sc, const DevFrame& f
         if (gl && gr) {
             const int nearc = tl <= tr ? n.d.x : n.d.y;
             const int farc = tl <= tr ? n.d.y : n.d.x;
-            if (sp < MCEV_STACK) stack[sp++] = farc;
+            if (sp < MCEV_STACK) stack[SIDX(sp++)] = farc;
             else *err = 1;
             next = nearc;
         } else if (gl) {
@@ -449,7 +460,7 @@ __device__ __forceinline__ Hit closest_hit(const DevScene& sc, const DevFrame& f
         }
         if (next == -0x7fffffff) {
             if (sp == 0) break;
-            next = stack[--sp];
+            next = stack[SIDX(--sp)];
         }
         node = next;
     }
@@ -458,7 +469,7 @@ __device__ __forceinline__ Hit closest_hit(const DevScene& sc, const DevFrame& f
 
 __device__ __forceinline__ bool occluded(const DevScene& sc, const DevFrame& fr, f3 o, f3 d, float tmin, float tmax,
                                          int* err, int2& work) {
-    int stack[MCEV_STACK];
+    MCEV_DECLARE_STACK(stack);
     if (fr.n_inst == 0) return false;
     if (fr.tlas_is_leaf) {
         int root, oi;
@@ -489,7 +500,7 @@ __device__ __forceinline__ bool occluded(const DevScene& sc, const DevFrame& fr,
         const bool gr = (m & 2) && n.d.y >= 0;
         int next = -0x7fffffff;
         if (gl && gr) {
-            if (sp < MCEV_STACK) stack[sp++] = n.d.y;
+            if (sp < MCEV_STACK) stack[SIDX(sp++)] = n.d.y;
             else *err = 1;
             next = n.d.x;
         } else if (gl) {
@@ -499,7 +510,7 @@ __device__ __forceinline__ bool occluded(const DevScene& sc, const DevFrame& fr,
         }
         if (next == -0x7fffffff) {
             if (sp == 0) return false;
-            next = stack[--sp];
+            next = stack[SIDX(--sp)];
         }
         node = next;
     }

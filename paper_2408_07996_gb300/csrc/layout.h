@@ -26,8 +26,16 @@
 #define MCEV_HD
 #endif
 
-// traversal stack entries per thread (TLAS + BLAS depth must fit)
+// Traversal stack per thread (TLAS + BLAS depth must fit): in shared memory
+// (32 entries, thread-interleaved) when MCEV_SMEM_STACK, else in local memory.
+#ifndef MCEV_SMEM_STACK
+#define MCEV_SMEM_STACK 0
+#endif
+#if MCEV_SMEM_STACK
+#define MCEV_STACK_HOST 32
+#else
 #define MCEV_STACK_HOST 96
+#endif
 
 namespace mcev {
 
