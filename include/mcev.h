@@ -6,7 +6,7 @@
  * describes: per pixel it path-traces log luminance samples at two times,
  * keeps their running mean and variance, runs a one-tailed Student t-test of
  * whether the log-brightness gap is below the event threshold (Sec. 3.2,
- * Eq. 5), re-queues only the undecided pixels for another batch of paths
+ * Eq. 7), re-queues only the undecided pixels for another batch of paths
  * (Sec. 3.3) and emits an event with its polarity where the gap exceeds the
  * threshold (Alg. 1, Eq. 1).
  *
@@ -51,7 +51,7 @@ enum {
     MCEV_MEAN_ONLY = 2,     /* ablation: stop iff |mu_b - mu_a| < C */
     MCEV_UNIFORM = 3        /* baseline: every pixel to spp_max, same event rule */
 };
-/* Standard error of Eq. 5: the paper's sqrt((s_a^2 + s_b^2) / n_b), or Welch's
+/* Standard error of Eq. 7: the paper's sqrt((s_a^2 + s_b^2) / n_b), or Welch's
  * sqrt(s_a^2 / n_a + s_b^2 / n_b). */
 enum { MCEV_SE_PAPER = 0, MCEV_SE_WELCH = 1 };
 
@@ -178,7 +178,7 @@ mcev_status mcev_render_reference(mcev_ctx* ctx, double t0, int32_t spp);
  * valid or was last set for a time other than t0, the reference is first
  * rendered at t0 with spp_max samples.  Then every pixel is sampled at t1
  * in a first batch of params.spp_min samples and further batches of
- * spp_batch, the t-test (Eq. 5 with the chosen variant and standard error)
+ * spp_batch, the t-test (Eq. 7 with the chosen variant and standard error)
  * deciding after each batch whether the pixel stops, up to spp_max.  A
  * decided pixel with |mean_t1 - mean_ref| > C gets event sign(gap) and its
  * statistics become the new reference (Alg. 1); the reference time becomes t1.

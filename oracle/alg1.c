@@ -5,7 +5,7 @@
  *    capped at spp_max (Sec. 3.3: first test at 256, then +64, cap 4096);
  *  - after each batch that leaves n < spp_max, the mean and the unbiased
  *    variance of all n log-luminance samples are recomputed (calcMeanVar);
- *  - t = (|mu_b - mu_a| - C) / sqrt((s_a^2 + s_b^2) / n_b)  (Eq. 5, N = n_b);
+ *  - t = (|mu_b - mu_a| - C) / sqrt((s_a^2 + s_b^2) / n_b)  (Eq. 7, N = n_b);
  *    the Welch form sqrt(s_a^2/n_a + s_b^2/n_b) is the optional se_mode;
  *  - one-tailed test towards "gap below C": stop sampling iff
  *    F_{n_b - 1}(t) < alpha (Sec. 3.2), F the Student t CDF;

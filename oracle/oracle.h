@@ -12,9 +12,9 @@
  *   - tracePaths(q, s, N) [Sec. 3, Alg. 1]: N unidirectional path-traced
  *     radiance samples of pixel q at time s (next-event estimation and
  *     power-heuristic MIS, as in pbrt-v4's PathIntegrator [Sec. 3.3]);
- *   - per-path log luminance y = ln(L + eps) [Sec. 3.1, Eq. 2] and its sample
- *     mean and unbiased variance [Eq. 2-3, calcMeanVar of Alg. 1];
- *   - the t-value [Eq. 5] and the one-tailed Student t-test [Sec. 3.2]
+ *   - per-path log luminance y = ln(L + eps) [Sec. 3.1, Eq. 3] and its sample
+ *     mean and unbiased variance [Eq. 3-4, calcMeanVar of Alg. 1];
+ *   - the t-value [Eq. 7] and the one-tailed Student t-test [Sec. 3.2]
  *     with the sampling schedule of Sec. 3.3 (first test at spp_min, then
  *     every spp_batch samples, cap spp_max);
  *   - event emission and reference update [Alg. 1, Eq. 1].
@@ -104,7 +104,7 @@ typedef struct {
     int32_t variant, se_mode;
 } orc_detect;
 
-/* sample mean and unbiased variance of y[0..n), two passes (Eq. 2-3) */
+/* sample mean and unbiased variance of y[0..n), two passes (Eq. 3-4) */
 void orc_mean_var(const double* y, int64_t n, double* mean, double* var);
 
 /* samples k0..k0+count-1 of one pixel as y = ln(L + eps) */

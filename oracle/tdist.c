@@ -1,4 +1,4 @@
-/* Student t distribution for the one-tailed test of Sec. 3.2 (Eq. 5).
+/* Student t distribution for the one-tailed test of Sec. 3.2 (Eq. 7).
  * Test infrastructure only.
  *
  * F_nu(t) = 1/2 I_x(nu/2, 1/2) for t < 0 and 1 - 1/2 I_x(nu/2, 1/2) for

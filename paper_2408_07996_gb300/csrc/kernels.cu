@@ -4,8 +4,8 @@
 //   raygen -> [extend -> shade(+NEE) -> shadow] x (max_depth + 1) -> stats
 // where extend/shade/shadow consume device-side ray queues (sizes in device
 // counters, no host round trip) and `stats` fuses, per queued pixel, the
-// log-luminance batch statistics (Sec. 3.1, Eq. 2-3), the Chan merge into the
-// running statistics, the t-test of Eq. 5 (Sec. 3.2), the warp-aggregated
+// log-luminance batch statistics (Sec. 3.1, Eq. 3-4), the Chan merge into the
+// running statistics, the t-test of Eq. 7 (Sec. 3.2), the warp-aggregated
 // re-queue of undecided pixels (Sec. 3.3) and the event rule with the
 // reference update (Alg. 1, Eq. 1).
 #include <cuda_runtime.h>

@@ -1,4 +1,4 @@
-// tdist.h -- Student t critical values for the test of Eq. 5 (host, FP64).
+// tdist.h -- Student t critical values for the test of Eq. 7 (host, FP64).
 #pragma once
 
 namespace mcev {

@@ -17,7 +17,7 @@ def det(**kw):
 
 
 def test_t_value_is_one_sample_t_when_reference_is_exact():
-    # With s_a^2 = 0 the t-value of Eq. 5 is the one-sample t statistic of the
+    # With s_a^2 = 0 the t-value of Eq. 7 is the one-sample t statistic of the
     # gaps y - mu_a against the threshold C, with n_b - 1 degrees of freedom.
     rng = np.random.default_rng(10)
     d = det(spp_min=64, spp_batch=64, spp_max=512)
@@ -41,7 +41,7 @@ def test_t_value_is_one_sample_t_when_reference_is_exact():
 def test_t_value_uses_both_variances_over_n_b():
     # With n_a = n_b the paper's standard error sqrt((s_a^2 + s_b^2)/N) equals
     # Welch's sqrt(s_a^2/n_a + s_b^2/n_b); scipy's Welch statistic on
-    # (y_b - C, y_a) is then the t-value of Eq. 5.
+    # (y_b - C, y_a) is then the t-value of Eq. 7.
     rng = np.random.default_rng(11)
     n = 32
     d = det(spp_min=n, spp_batch=n, spp_max=4 * n)
