@@ -46,7 +46,51 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--crop", type=int, default=24, help="oracle crop side (pixels)")
     ap.add_argument("--wavefront", type=int, default=0)
+    ap.add_argument("--profile-band", type=int, nargs=3, metavar=("ROW0", "ROW1", "SPP"),
+                    help="only trace SPP samples of every pixel in image rows [ROW0, ROW1) at keyframe 3 "
+                         "(a small, representative case for kernel captures) and exit")
     return ap.parse_args()
+
+
+def profile_band(args):
+    """tracePaths over one band of image rows: the first launches of the
+    process are full-size raygen / extend / shade / shadow launches."""
+    import torch
+
+    import scenegen as sg
+    from paper_2408_07996_gb300.api import Renderer
+    w = sg.workload(args.workload)
+    r = Renderer(w.width, w.height, 0)
+    r.upload(w.scene)
+    r.configure(w)
+    r.set_params(wavefront=args.wavefront)
+    r0, r1, spp = args.profile_band
+    pix = torch.arange(r0 * w.width, r1 * w.width, dtype=torch.int32, device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    L, _ = r.trace_samples(w.times[3], pix, 0, spp, want_sig=False)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    print(json.dumps({"profile_band": [r0, r1, spp], "paths": int(L.numel()), "ms": ms,
+                      "mpaths_per_s": L.numel() / ms / 1e3}), flush=True)
+    r.close()
+
+
+# ------------------------------------------------------------------ multi-rank aggregation
+def max_over_ranks(x: float, dist=None, device="cpu") -> float:
+    """The largest value of x over all ranks (the job's time is its slowest rank's)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, seconds: float, world: int) -> float:
+    """Whole-job throughput: every rank's units over the slowest rank's time."""
+    return units_per_rank * world / seconds
 
 
 # ------------------------------------------------------------------ clocks
@@ -178,6 +222,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_band:
+        return profile_band(args)
     import numpy as np
     import torch
 
@@ -216,8 +262,10 @@ def main():
                                spp_max or w.spp_max, out=out)
 
     # warm-up: the first frame renders the reference at t0 (Alg. 1 first frame)
+    pre_launches = 0
     for k in range(Wm):
-        frame(k)
+        pre_launches += frame(k)["stats"]["kernel_launches"]
+    print(f"[bench] launches before the timed loop: {pre_launches}", file=sys.stderr, flush=True)
     torch.cuda.synchronize()
     state0 = r.get_state().clone()
 
@@ -234,18 +282,14 @@ def main():
     torch.cuda.synchronize()
     clk = clocks.stop()
     barrier()
-    ms = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    frames_per_s = K * world / (ms / 1e3)
+    ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
+    frames_per_s = job_rate(K, ms / 1e3, world)
     for s_ in steps:
         print(f"[bench] step: {s_['gpu_ms']:.1f} ms, {s_['paths']} paths, {s_['rounds']} rounds, "
               f"events {s_['events_pos']}+{s_['events_neg']}, kernel ms {[round(x, 1) for x in s_['kernel_ms']]}",
               file=sys.stderr, flush=True)
     paths = sum(s["paths"] for s in steps)
-    mpaths = paths * world / (ms / 1e3) / 1e6
+    mpaths = job_rate(paths, ms / 1e3, world) / 1e6
     launches = sum(s["kernel_launches"] for s in steps)
 
     # roofline of the dominant kernel (closest-hit traversal), from the
@@ -337,12 +381,8 @@ def main():
             torch.cuda.current_stream().synchronize()
             h2d += o["stats"]["h2d_bytes"]
             d2h += o["stats"]["d2h_bytes"] + sum(v.numel() * v.element_size() for v in host.values())
-        dt = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([dt], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
-        line["e2e"] = {"value": K * world / dt, "unit": "event frames/s", "h2d_bytes_per_step": h2d / K,
+        dt = max_over_ranks(time.perf_counter() - t0, dist, dev)
+        line["e2e"] = {"value": job_rate(K, dt, world), "unit": "event frames/s", "h2d_bytes_per_step": h2d / K,
                        "d2h_bytes_per_step": d2h / K}
 
     r.close()

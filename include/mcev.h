@@ -196,7 +196,7 @@ mcev_status mcev_render_events(mcev_ctx* ctx, double t0, double t1, float C, flo
 
 /* tracePaths(q, s, N) of Alg. 1: path-traced radiance of samples
  * k0 .. k0+count-1 of each listed pixel at time t.
- *   pixels : device int32 [n_pix], values in [0, H*W)
+ *   pixels : device int32 [n_pix], values in [0, H*W) (may be NULL when n_pix = 0)
  *   L_out  : device float [n_pix][count]
  *   sig_out: device uint32 [n_pix][count] or NULL: FNV-1a hash of every
  *            discrete decision along the path (hit instance/triangle ids,

@@ -1077,9 +1077,10 @@ mcev_status mcev_render_events(mcev_ctx* ctx, double t0, double t1, float C, flo
 mcev_status mcev_trace_samples(mcev_ctx* ctx, double t, const int32_t* pixels, int64_t n_pix, int64_t k0,
                                int32_t count, float* L_out, uint32_t* sig_out) {
     ST(check_ready(ctx));
-    if (!pixels || !L_out || n_pix < 0 || k0 < 0 || count < 1 || k0 + count > ((int64_t)1 << 32))
-        return fail(ctx, MCEV_ERR_ARG, "bad trace_samples arguments");
+    if (n_pix < 0 || k0 < 0 || count < 1 || k0 + count > ((int64_t)1 << 32))
+        return fail(ctx, MCEV_ERR_ARG, "bad trace_samples sizes");
     if (n_pix == 0) return MCEV_OK;
+    if (!pixels || !L_out) return fail(ctx, MCEV_ERR_ARG, "null pixels or L_out");
     reset_call_counters(ctx);
     ST(frame_setup(ctx, t, 0));
     const DevParams P = dev_params(ctx, sig_out != nullptr);

@@ -18,6 +18,11 @@ MEAN_TOL = 1e-4      # per-pixel mean ln L, absolute (spec tolerance)
 T_BAND = 1e-3        # |t - t_crit| band where FP32/FP64 decisions may differ
 C_BAND = 1e-5        # | |gap| - C | band
 SAMPLE_MISMATCH = 2e-3   # max fraction of samples with different discrete decisions
+# Per-sample ln L on samples with identical decisions: FP32 paths have heavy
+# but rare tails (grazing cosines, near-polar environment directions), so the
+# bar is on the 99.9th percentile, with a loose cap on the maximum.
+SAMPLE_P999 = 1e-4
+SAMPLE_MAX = 1e-2
 
 
 @pytest.fixture(scope="module")
@@ -64,7 +69,7 @@ def test_cornell_per_sample_parity(cornell, t):
     s = summary(ps)
     print("cornell per-sample", t, s)
     assert s["mismatch"] <= SAMPLE_MISMATCH
-    assert s["max_dy"] < 1e-3
+    assert s["p999_dy"] < SAMPLE_P999 and s["max_dy"] < SAMPLE_MAX
     # per-pixel means over pixels whose every sample made the same decisions
     full = ps["match"].all(axis=1)
     dm = np.abs(ps["yg"].mean(1) - ps["yo"].mean(1))[full]
@@ -196,3 +201,152 @@ def test_errors_are_statuses_not_crashes():
     with pytest.raises(McevError, match="ARG"):
         r.upload(bad)
     r.close()
+
+
+# ---------------------------------------------------------------- larger scenes
+
+@pytest.fixture(scope="module")
+def spheres():
+    w = sg.workload("spheres512")
+    return w, O.OracleScene(w.scene)
+
+
+@pytest.fixture(scope="module")
+def terrain():
+    w = sg.workload("terrain720p")
+    return w, O.OracleScene(w.scene)
+
+
+@pytest.mark.parametrize("k", [0, 5])
+def test_spheres_per_sample_parity(spheres, k):
+    # keyframe 5 has the spinning sphere turned; pixels span the whole image
+    w, osc = spheres
+    r = renderer_for(w)
+    rng = np.random.default_rng(40 + k)
+    pix = np.sort(rng.choice(w.width * w.height, size=1500, replace=False))
+    ps = per_sample(r, osc, O.params_of(w), w.times[k], pix, 0, 24, w.eps)
+    s = summary(ps)
+    print("spheres per-sample", k, s)
+    assert s["mismatch"] <= SAMPLE_MISMATCH
+    assert s["p999_dy"] < SAMPLE_P999 and s["max_dy"] < SAMPLE_MAX
+    full = ps["match"].all(axis=1)
+    assert np.abs(ps["yg"].mean(1) - ps["yo"].mean(1))[full].max() < MEAN_TOL
+    r.close()
+
+
+def test_terrain_per_sample_parity(terrain):
+    w, osc = terrain
+    r = renderer_for(w)
+    rng = np.random.default_rng(41)
+    pix = np.sort(rng.choice(w.width * w.height, size=1200, replace=False))
+    ps = per_sample(r, osc, O.params_of(w), w.times[3], pix, 100, 16, w.eps)
+    s = summary(ps)
+    print("terrain per-sample", s)
+    assert s["mismatch"] <= SAMPLE_MISMATCH
+    assert s["p999_dy"] < SAMPLE_P999 and s["max_dy"] < SAMPLE_MAX
+    full = ps["match"].all(axis=1)
+    assert np.abs(ps["yg"].mean(1) - ps["yo"].mean(1))[full].max() < MEAN_TOL
+    r.close()
+
+
+@pytest.mark.slow
+def test_terrain_full_frame_sampled_pixels(terrain):
+    """The benchmark's configuration at full size (1280x720, 8192-spp
+    reference, 512/+64/8192 schedule, 32M-path wavefront), checked on
+    sampled pixels the oracle recomputes one by one."""
+    w, osc = terrain
+    r = renderer_for(w)
+    out = r.render_events(w.times[0], w.times[1], w.C, w.alpha, w.spp_batch, w.spp_max)
+    ev = out["events"].cpu().numpy().reshape(-1)
+    n = out["spp"].cpu().numpy().reshape(-1)
+    mean = out["mean"].cpu().numpy().reshape(-1)
+    rng = np.random.default_rng(42)
+    evpix = np.flatnonzero(ev != 0)
+    pix = np.unique(np.concatenate([rng.choice(w.width * w.height, size=112, replace=False),
+                                    rng.choice(evpix, size=min(32, evpix.size), replace=False)])).astype(np.int32)
+    p, det = O.params_of(w), O.detect_of(w)
+    ref = O.render_events(osc, p, det, w.times[0], w.times[1], pix)
+    s0 = per_sample(r, osc, p, w.times[0], pix, 0, w.spp_max, w.eps)
+    k1 = int(max(n[pix].max(), ref["n"].max()))
+    s1 = per_sample(r, osc, p, w.times[1], pix, 0, k1, w.eps)
+    used1 = np.arange(k1)[None, :] < np.maximum(n[pix], ref["n"])[:, None]
+    m0 = s0["match"].all(1)
+    m1 = np.where(used1, s1["match"], True).all(1)
+    q = 1 - np.concatenate([s0["match"].reshape(-1), s1["match"][used1]]).mean()
+    keep = m0 & m1 & (ref["margin_t"] >= T_BAND) & (ref["margin_c"] >= C_BAND)
+    print("terrain full frame: sample mismatch %.2e, kept %d of %d sampled pixels" % (q, keep.sum(), pix.size))
+    assert q <= SAMPLE_MISMATCH
+    # each sampled pixel draws ~(spp_max + n) samples; it is set aside when
+    # any of them took a different discrete decision in FP32 and FP64
+    expect_kept = np.mean((1 - q) ** (w.spp_max + np.maximum(n[pix], ref["n"])))
+    assert keep.mean() >= 0.5 * expect_kept and keep.sum() >= 10
+    assert (ev[pix] == ref["events"])[keep].all()
+    assert (n[pix] == ref["n"])[keep].all()
+    assert np.abs(mean[pix] - ref["mean"])[keep].max() < MEAN_TOL
+    st = out["stats"]
+    assert st["ref_paths"] == w.width * w.height * w.spp_max
+    assert st["paths"] == int(n.sum())
+    r.close()
+
+
+# ---------------------------------------------------------------- edge cases
+
+@pytest.mark.parametrize("case", [
+    dict(spp_min=32, spp_batch=32, spp_max=32),     # a single batch, no test
+    dict(spp_min=16, spp_batch=40, spp_max=200),    # ragged last batch
+    dict(C=0.0),                                    # every pixel to the cap
+    dict(se_mode=O.SE_WELCH),
+    dict(alpha=0.5),
+])
+def test_small_frame_edge_cases(cornell, case):
+    w0, osc = cornell
+    w = sg.workload("cornell64")
+    W = H = 16
+    kw = dict(case)
+    se = kw.pop("se_mode", O.SE_PAPER)
+    for k, v in kw.items():
+        setattr(w, k, v)
+    r = renderer_for(w, width=W, height=H, se_mode=se)
+    p = O.params_of(w, width=W, height=H)
+    det = O.detect_of(w, se_mode=se)
+    res = _event_parity(r, osc, w, det, 0.0, 1.0, H, W, p)
+    assert res["bad_ev"].sum() == 0 and res["bad_n"].sum() == 0
+    assert res["dmean"].max() < MEAN_TOL
+    n = res["n"]
+    allowed = {min(w.spp_min + w.spp_batch * j, w.spp_max) for j in range(w.spp_max)}
+    assert set(np.unique(n)) <= allowed
+    if w.C == 0.0:
+        assert (n == w.spp_max).all()
+    r.close()
+
+
+def test_trace_samples_empty_and_ragged(cornell):
+    w, osc = cornell
+    r = renderer_for(w, wavefront=1024)
+    L, sig = r.trace_samples(0.0, torch.zeros(0, dtype=torch.int32), 0, 8)
+    assert L.shape == (0, 8)
+    pix = np.array([0, 63, 4095, 2080, 17], np.int32)
+    ps = per_sample(r, osc, O.params_of(w), 0.5, pix, 1000, 333, w.eps)   # chunks of 3 pixels
+    assert summary(ps)["mismatch"] <= SAMPLE_MISMATCH
+    r.close()
+
+
+def test_allocation_failure_is_reported():
+    # the allocator hook is how a host framework supplies memory; a NULL
+    # from it must surface as MCEV_ERR_OOM, not a crash
+    import ctypes as C
+    from paper_2408_07996_gb300 import _lib as L
+    lib = L.load()
+    ctx = C.c_void_p()
+    assert lib.mcev_create(C.byref(ctx), 0, 8, 8) == 0
+    alloc = L.ALLOC_FN(lambda n, u: None)
+    free = L.FREE_FN(lambda p, u: None)
+    assert lib.mcev_set_allocator(ctx, alloc, free, None) == 0
+    from paper_2408_07996_gb300.api import Renderer  # noqa: F401  (desc builder below)
+    sc = sg.cornell_box()
+    import paper_2408_07996_gb300.api as api
+    r = api.Renderer.__new__(api.Renderer)
+    r.lib, r.ctx = lib, ctx
+    with pytest.raises(L.McevError, match="OOM"):
+        api.Renderer.upload(r, sc)
+    lib.mcev_destroy(ctx)
