@@ -105,7 +105,10 @@ typedef struct {
     uint64_t seed;      /* Philox key seed */
     int64_t wavefront;  /* max paths in flight per chunk; 0 = library default */
     int32_t profile;    /* 1: time every kernel launch with CUDA events (mcev_stats.kernel_ms) */
-    int32_t reserved;   /* must be 0 */
+    int32_t batch_window; /* after the first batch, a round may trace up to this many batches of
+                             spp_batch per undecided pixel at once (as many as fill the wavefront),
+                             merging and testing them in order; samples after a pixel's decision
+                             are unused.  1 = one batch per round; 0 = library default (16). */
 } mcev_params;
 
 /* kernel classes reported in mcev_stats */
@@ -115,6 +118,7 @@ enum { MCEV_K_RAYGEN = 0, MCEV_K_EXTEND = 1, MCEV_K_SHADE = 2, MCEV_K_SHADOW = 3
 /* Per-call counters (mcev_render_events, optional). */
 typedef struct {
     int64_t paths;          /* path samples traced for the t1 frame */
+    int64_t samples_used;   /* samples that entered the decisions (sum of per-pixel counts) */
     int64_t ref_paths;      /* path samples traced for a t0 reference frame (0 if reused) */
     int32_t rounds;         /* batch rounds at t1 */
     int32_t kernel_launches;/* kernels launched by this call */

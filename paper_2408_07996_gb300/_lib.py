@@ -41,13 +41,13 @@ class Params(C.Structure):
     _fields_ = [
         ("eps", C.c_float), ("t_min", C.c_float), ("max_depth", C.c_int32), ("nee", C.c_int32),
         ("mis", C.c_int32), ("spp_min", C.c_int32), ("variant", C.c_int32), ("se_mode", C.c_int32),
-        ("seed", C.c_uint64), ("wavefront", C.c_int64), ("profile", C.c_int32), ("reserved", C.c_int32),
+        ("seed", C.c_uint64), ("wavefront", C.c_int64), ("profile", C.c_int32), ("batch_window", C.c_int32),
     ]
 
 
 class Stats(C.Structure):
     _fields_ = [
-        ("paths", C.c_int64), ("ref_paths", C.c_int64), ("rounds", C.c_int32),
+        ("paths", C.c_int64), ("samples_used", C.c_int64), ("ref_paths", C.c_int64), ("rounds", C.c_int32),
         ("kernel_launches", C.c_int32), ("events_pos", C.c_int64), ("events_neg", C.c_int64),
         ("pixels_at_cap", C.c_int64), ("nonfinite", C.c_int64), ("gpu_ms", C.c_double),
         ("nodes_closest", C.c_int64), ("tris_closest", C.c_int64), ("nodes_shadow", C.c_int64),

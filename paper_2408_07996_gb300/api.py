@@ -35,6 +35,7 @@ class RenderSettings:
     seed: int = 20240815
     wavefront: int = 0
     profile: int = 0
+    batch_window: int = 0
 
 
 class Renderer:
@@ -145,7 +146,7 @@ class Renderer:
         s = self.settings
         p = L.Params(eps=s.eps, t_min=s.t_min, max_depth=s.max_depth, nee=s.nee, mis=s.mis,
                      spp_min=s.spp_min, variant=s.variant, se_mode=s.se_mode, seed=s.seed,
-                     wavefront=s.wavefront, profile=s.profile, reserved=0)
+                     wavefront=s.wavefront, profile=s.profile, batch_window=s.batch_window)
         L.check(self.lib.mcev_set_params(self.ctx, C.byref(p)), self.ctx, "mcev_set_params")
         return s
 

@@ -719,11 +719,24 @@ mcev_status run_rounds(mcev_ctx* ctx, const Frame& fr, StatsArgs A, int64_t* pat
     int64_t Q = npix, n_done = 0, paths = 0;
     int rounds = 0, qi = 0;
     int32_t h_count = 0;
+    const int64_t window_max = ctx->params.batch_window > 0 ? ctx->params.batch_window : 16;
     while (Q > 0) {
-        const int32_t spp_r = n_done == 0 ? std::min(A.spp_min, A.spp_max)
-                                          : (int32_t)std::min<int64_t>(A.spp_batch, A.spp_max - n_done);
+        // first round: spp_min samples; later rounds: a window of m batches
+        // of spp_batch, as many as fill the wavefront (speculative samples of
+        // pixels that decide inside the window are traced but not used)
+        int32_t spp_r, sub;
+        if (n_done == 0) {
+            spp_r = sub = std::min(A.spp_min, A.spp_max);
+        } else {
+            sub = A.spp_batch;
+            const int64_t left = (A.spp_max - n_done + sub - 1) / sub;
+            int64_t m = std::max<int64_t>(1, ctx->wave.cap / std::max<int64_t>(1, Q * sub));
+            m = std::min(std::min(m, left), window_max);
+            spp_r = (int32_t)std::min<int64_t>(m * sub, A.spp_max - n_done);
+        }
         CU(cudaMemsetAsync(ctx->wave.counters + 3, 0, sizeof(int32_t), ctx->stream));
         A.spp_r = spp_r;
+        A.sub = sub;
         A.k_base = n_done;
         const int64_t per_chunk = std::max<int64_t>(1, ctx->wave.cap / spp_r);
         for (int64_t j0 = 0; j0 < Q; j0 += per_chunk) {
@@ -982,13 +995,13 @@ mcev_status mcev_set_params(mcev_ctx* ctx, const mcev_params* p) {
     if (!p) return fail(ctx, MCEV_ERR_ARG, "null params");
     if (!(p->eps > 0.0f) || !(p->t_min >= 0.0f) || p->max_depth < 0 || p->max_depth > 64 || p->spp_min < 2 ||
         p->variant < 0 || p->variant > 3 || p->se_mode < 0 || p->se_mode > 1 || p->wavefront < 0 ||
+        p->batch_window < 0 || p->batch_window > 1024 ||
         (p->wavefront > 0 && p->wavefront < 1024) || p->wavefront > ((int64_t)1 << 30))
         return fail(ctx, MCEV_ERR_ARG, "invalid render parameters");
     const bool reseed = p->seed != ctx->params.seed;
     const bool shape = p->eps != ctx->params.eps || p->t_min != ctx->params.t_min ||
                        p->max_depth != ctx->params.max_depth || p->nee != ctx->params.nee || p->mis != ctx->params.mis;
     ctx->params = *p;
-    if (p->reserved != 0) return fail(ctx, MCEV_ERR_ARG, "reserved field must be 0");
     if (reseed || shape) {
         ctx->ref_valid = false;
         for (auto& f : ctx->frames) f.valid = false;
@@ -1049,6 +1062,7 @@ mcev_status mcev_render_events(mcev_ctx* ctx, double t0, double t1, float C, flo
         std::memcpy(u, c + 32, sizeof u);
         std::memset(stats_out, 0, sizeof *stats_out);
         stats_out->paths = paths;
+        stats_out->samples_used = (int64_t)u[6];
         stats_out->ref_paths = ref_paths;
         stats_out->rounds = rounds;
         stats_out->kernel_launches = ctx->launches;

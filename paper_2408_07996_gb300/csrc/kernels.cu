@@ -325,46 +325,79 @@ __global__ void __launch_bounds__(256) k_stats(Wave w, StatsArgs A, const int32_
             if (lane == 0) atomicOr(w.counters + 8, 1);
             continue;
         }
-        // per-lane Welford over the lane's samples of this batch
-        Moments m{0.0f, 0.0f, 0.0f};
+        // The round traced spp_r samples of this pixel: one batch, or a window
+        // of several spp_batch-sized batches.  Each batch is merged and tested
+        // in order exactly as Alg. 1 would; once the pixel is decided, the
+        // rest of the window is left unused.  Every lane computes the same
+        // statistics (butterfly merges in a fixed order), so the decisions
+        // are warp-uniform.
+        Moments c{0.0f, 0.0f, 0.0f};
+        if (A.k_base > 0) c = Moments{(float)A.cur.n[pix], A.cur.mean[pix], A.cur.m2[pix]};
+        const bool detect = A.mode == MODE_DETECT;
+        const float ma = detect ? A.ref.mean[pix] : 0.0f;
+        const int32_t na = detect ? A.ref.n[pix] : 0;
+        const float va = (detect && na > 1) ? A.ref.m2[pix] / (float)(na - 1) : 0.0f;
         int bad = 0;
+        bool decided = false;
+        int32_t n = (int32_t)c.n;
         const float* Lp = w.L + j * A.spp_r;
-        for (int s = lane; s < A.spp_r; s += 32) {
-            float Lv = Lp[s];
-            if (!isfinite(Lv)) {
-                Lv = 0.0f;
-                ++bad;
+        for (int s0 = 0; s0 < A.spp_r && !decided; s0 += A.sub) {
+            const int s1 = min(s0 + A.sub, A.spp_r);
+            // per-lane Welford over the lane's samples of this batch
+            Moments m{0.0f, 0.0f, 0.0f};
+            for (int s = s0 + lane; s < s1; s += 32) {
+                float Lv = Lp[s];
+                if (!isfinite(Lv)) {
+                    Lv = 0.0f;
+                    ++bad;
+                }
+                const float y = logf(Lv + A.eps);
+                m.n += 1.0f;
+                const float dl = y - m.mean;
+                m.mean += dl / m.n;
+                m.m2 += dl * (y - m.mean);
             }
-            const float y = logf(Lv + A.eps);
-            m.n += 1.0f;
-            const float dl = y - m.mean;
-            m.mean += dl / m.n;
-            m.m2 += dl * (y - m.mean);
-        }
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            Moments o;
-            o.n = __shfl_xor_sync(0xffffffffu, m.n, off);
-            o.mean = __shfl_xor_sync(0xffffffffu, m.mean, off);
-            o.m2 = __shfl_xor_sync(0xffffffffu, m.m2, off);
-            // merge in a fixed lane order so every lane gets identical bits
-            m = (lane & off) ? chan(o, m) : chan(m, o);
+            for (int off = 16; off > 0; off >>= 1) {
+                Moments o;
+                o.n = __shfl_xor_sync(0xffffffffu, m.n, off);
+                o.mean = __shfl_xor_sync(0xffffffffu, m.mean, off);
+                o.m2 = __shfl_xor_sync(0xffffffffu, m.m2, off);
+                // merge in a fixed lane order so every lane gets identical bits
+                m = (lane & off) ? chan(o, m) : chan(m, o);
+            }
+            c = (A.k_base == 0 && s0 == 0) ? m : chan(c, m);
+            n = (int32_t)c.n;
+            if (!detect) continue;
+            decided = n >= A.spp_max;
+            if (!decided && A.variant != VAR_UNIFORM) {
+                const float gap = fabsf(c.mean - ma);
+                if (A.variant == VAR_MEAN_ONLY) {
+                    decided = gap < A.C;
+                } else {
+                    const float vb = c.m2 / (float)(n - 1);
+                    const float se2 = A.se_mode == SE_WELCH ? va / (float)na + vb / (float)n : (va + vb) / (float)n;
+                    if (se2 == 0.0f) {
+                        decided = gap < A.C;
+                    } else if (kChecked && n < A.spp_min) {
+                        decided = false;
+                    } else {
+                        const float t = (gap - A.C) / sqrtf(se2);
+                        int r = (n - A.spp_min) / A.spp_batch;
+                        if (kChecked) r = min(r, (A.spp_max - A.spp_min + A.spp_batch - 1) / A.spp_batch - 1);
+                        const float tc = __ldg(A.tcrit + r);
+                        decided = A.variant == VAR_TWO_TAILED ? (t < tc || t > -tc) : (t < tc);
+                    }
+                }
+            }
         }
         bad = __reduce_add_sync(0xffffffffu, bad);
         if (lane != 0) continue;
         if (bad) atomicAdd(w.counters + 4, bad);
-        Moments c;
-        if (A.k_base == 0) {
-            c = m;
-        } else {
-            Moments prev{(float)A.cur.n[pix], A.cur.mean[pix], A.cur.m2[pix]};
-            c = chan(prev, m);
-        }
-        const int32_t n = (int32_t)c.n;
         A.cur.n[pix] = n;
         A.cur.mean[pix] = c.mean;
         A.cur.m2[pix] = c.m2;
-        if (A.mode == MODE_REFERENCE) {
+        if (!detect) {
             if (n >= A.spp_max) {
                 A.ref.n[pix] = n;
                 A.ref.mean[pix] = c.mean;
@@ -373,30 +406,6 @@ __global__ void __launch_bounds__(256) k_stats(Wave w, StatsArgs A, const int32_
                 next_queue[atomicAdd(w.counters + 3, 1)] = pix;
             }
             continue;
-        }
-        const float ma = A.ref.mean[pix];
-        bool decided = n >= A.spp_max;
-        if (!decided && A.variant != VAR_UNIFORM) {
-            const float gap = fabsf(c.mean - ma);
-            if (A.variant == VAR_MEAN_ONLY) {
-                decided = gap < A.C;
-            } else {
-                const int32_t na = A.ref.n[pix];
-                const float va = na > 1 ? A.ref.m2[pix] / (float)(na - 1) : 0.0f;
-                const float vb = c.m2 / (float)(n - 1);
-                const float se2 = A.se_mode == SE_WELCH ? va / (float)na + vb / (float)n : (va + vb) / (float)n;
-                if (se2 == 0.0f) {
-                    decided = gap < A.C;
-                } else if (kChecked && n < A.spp_min) {
-                    decided = false;
-                } else {
-                    const float t = (gap - A.C) / sqrtf(se2);
-                    int r = (n - A.spp_min) / A.spp_batch;
-                    if (kChecked) r = min(r, (A.spp_max - A.spp_min + A.spp_batch - 1) / A.spp_batch - 1);
-                    const float tc = __ldg(A.tcrit + r);
-                    decided = A.variant == VAR_TWO_TAILED ? (t < tc || t > -tc) : (t < tc);
-                }
-            }
         }
         if (!decided) {
             next_queue[atomicAdd(w.counters + 3, 1)] = pix;
@@ -412,6 +421,7 @@ __global__ void __launch_bounds__(256) k_stats(Wave w, StatsArgs A, const int32_
             atomicAdd(w.counters + (ev > 0 ? 5 : 6), 1);
         }
         if (n >= A.spp_max) atomicAdd(w.counters + 7, 1);
+        atomicAdd(reinterpret_cast<unsigned long long*>(w.counters + 32) + 6, (unsigned long long)n);
         A.events[pix] = ev;
         if (A.spp_out) A.spp_out[pix] = n;
         if (A.mean_out) A.mean_out[pix] = c.mean;
@@ -597,6 +607,7 @@ extern "C" mcev_status mcev_detect_batch_static(const mcev_detect_args* a, int64
     A.eps = a->eps;
     A.C = a->C;
     A.spp_r = a->spp_r;
+    A.sub = a->spp_r;
     A.k_base = a->k_base;
     A.spp_min = a->spp_min;
     A.spp_batch = a->spp_batch;

@@ -18,8 +18,9 @@ struct StatsArgs {
     int32_t* spp_out;
     float* mean_out;
     float eps, C;
-    int32_t spp_r;        // samples per pixel in this batch
-    int64_t k_base;       // samples taken before this batch
+    int32_t spp_r;        // samples per pixel traced this round
+    int32_t sub;          // batch size: the round's samples are merged and tested in batches of `sub`
+    int64_t k_base;       // samples taken before this round
     int32_t spp_min, spp_batch, spp_max;
     int32_t mode, variant, se_mode;
     int64_t n_total;      // per-pixel array length, checked only by the allocation-free entry point
