@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--crop", type=int, default=24, help="oracle crop side (pixels)")
     ap.add_argument("--wavefront", type=int, default=0)
+    ap.add_argument("--no-tune", action="store_true", help="batch64: skip the autotuner")
     ap.add_argument("--profile-band", type=int, nargs=3, metavar=("ROW0", "ROW1", "SPP"),
                     help="only trace SPP samples of every pixel in image rows [ROW0, ROW1) at keyframe 3 "
                          "(a small, representative case for kernel captures) and exit")
@@ -217,6 +218,90 @@ def _config(w):
                   "are streamed every step"}
 
 
+# ------------------------------------------------------------------ batched jobs (config 4)
+def run_batch(args):
+    """64 independent frame pairs (image sizes from 128x128 to 640x480,
+    5k-100k triangles each) rendered in shared rounds; one step = one event
+    frame of every job.  The wavefront width, batch window and BVH leaf size
+    are picked by the autotuner on the first frame pair after warm-up."""
+    import torch
+
+    import scenegen as sg
+    from paper_2408_07996_gb300.api import Renderer, render_events_batch
+    from paper_2408_07996_gb300.autotune import tune_batch
+
+    ws = sg.batch_workloads(64)
+    rs = []
+    for w in ws:
+        r = Renderer(w.width, w.height)
+        r.upload(w.scene)
+        r.configure(w)
+        rs.append(r)
+    runner = Renderer(8, 8)
+    runner.set_params(profile=1)
+    sched = dict(C=ws[0].C, alpha=ws[0].alpha, spp_batch=ws[0].spp_batch, spp_max=ws[0].spp_max)
+    times = ws[0].times
+    K, Wm = args.steps, max(3, args.warmup)
+    assert Wm + K < len(times), "not enough keyframes"
+
+    def frame(k):
+        return render_events_batch(runner, [(r, times[k], times[k + 1]) for r in rs], *sched.values())
+
+    for k in range(Wm):
+        frame(k)
+    # autotune on the next frame pair of the first 16 jobs (their references
+    # exist, so a trial costs one adaptive frame); states are restored
+    tune = None
+    if not args.no_tune:
+        tune = tune_batch(runner, rs[:16], (times[Wm], times[Wm + 1]), sched,
+                          wavefronts=(1 << 23, 1 << 25), windows=(4, 16), leaf_sizes=(2, 4))
+        tune = {"best": tune["best"], "trials": len(tune["trials"]), "jobs": 16}
+    torch.cuda.synchronize()
+    clocks = Clocks(0)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    steps = [frame(k)[1] for k in range(Wm, Wm + K)]
+    e1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    paths = sum(s["paths"] for s in steps)
+    kms = [sum(s["kernel_ms"][i] for s in steps) for i in range(5)]
+    total = sum(kms)
+    line = {"metric": "event frames/s of 64 batched frame pairs (config 4)", "value": 64 * K / (ms / 1e3),
+            "unit": "event frames/s", "n_gpus": 1, "steps": K, "warmup": Wm, "ms_per_step": ms / K,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batch64", "jobs": 64, "pixels": sum(w.width * w.height for w in ws),
+                       "triangles": [min(w.scene.n_triangles for w in ws), max(w.scene.n_triangles for w in ws)],
+                       "resolutions": sorted({f"{w.width}x{w.height}" for w in ws}), **sched,
+                       "spp_min": ws[0].spp_min},
+            "mpaths_per_s": paths / (ms / 1e3) / 1e6, "rounds_per_step": sum(s["rounds"] for s in steps) / K,
+            "gpu_launches": sum(s["kernel_launches"] for s in steps),
+            "kernel_share": {n: round(kms[i] / total, 4) if total else None
+                             for i, n in enumerate(["raygen", "extend", "shade", "shadow", "stats"])},
+            "launch_gaps_ms_per_step": (sum(s["gpu_ms"] for s in steps) - total) / K,
+            "autotune": tune, "clocks": clk}
+    # the same frame rendered job after job (one-job batches through the same
+    # runner and wavefront) against all jobs in shared rounds
+    if not args.no_uniform:
+        k = Wm + K
+        states = [r.get_state().clone() for r in rs]
+        _, bst = frame(k)
+        for r, s0 in zip(rs, states):
+            r.set_state(s0)
+        seq_ms = 0.0
+        for r in rs:
+            _, st1 = render_events_batch(runner, [(r, times[k], times[k + 1])], *sched.values())
+            seq_ms += st1["gpu_ms"]
+        line["batched_vs_one_by_one"] = {"frame": k, "batched_ms": bst["gpu_ms"], "one_by_one_ms": seq_ms,
+                                         "speedup": seq_ms / bst["gpu_ms"]}
+    for r in rs:
+        r.close()
+    runner.close()
+    print(json.dumps(line), flush=True)
+
+
 # ------------------------------------------------------------------ our arm
 def main():
     args = parse()
@@ -224,6 +309,8 @@ def main():
         return run_reference(args)
     if args.profile_band:
         return profile_band(args)
+    if args.workload == "batch64":
+        return run_batch(args)
     import numpy as np
     import torch
 

@@ -198,6 +198,30 @@ mcev_status mcev_render_events(mcev_ctx* ctx, double t0, double t1, float C, flo
                                int32_t spp_batch, int32_t spp_max, int8_t* events_out,
                                int32_t* spp_out, float* mean_out, mcev_stats* stats_out);
 
+/* One frame pair of a batched render. */
+typedef struct {
+    mcev_ctx* ctx;          /* scene, camera, image size, settings and reference state of this job */
+    double t0, t1;          /* the frame pair, as in mcev_render_events */
+    int8_t* events_out;     /* device int8 [H*W] of ctx, required */
+    int32_t* spp_out;       /* device int32 [H*W] or NULL */
+    float* mean_out;        /* device float [H*W] or NULL */
+} mcev_job;
+
+/* Batched Alg. 1 frames: every job's frame pair is rendered exactly as
+ * mcev_render_events would render it on its own context (same samples, same
+ * decisions, same outputs and reference update), but all jobs' pixels share
+ * one queue of undecided pixels, one set of rounds and the same wavefront
+ * chunks, so many small frames (different scenes and image sizes) keep the
+ * GPU as busy as one large frame.  References missing at t0 are rendered
+ * first, also batched.  The runner context (which may also be one of the
+ * jobs' contexts) supplies the stream, allocator, wavefront buffers and the
+ * reported counters.  All jobs must share spp_min, variant and se_mode (the
+ * schedule); every other setting is per job.  Jobs must use distinct
+ * contexts on the runner's device, of at most 2^24 pixels each; n_jobs is
+ * 1..256.  Errors: ARG, STATE, OOM, CUDA. */
+mcev_status mcev_render_events_batch(mcev_ctx* runner, const mcev_job* jobs, int32_t n_jobs, float C, float alpha,
+                                     int32_t spp_batch, int32_t spp_max, mcev_stats* stats_out);
+
 /* tracePaths(q, s, N) of Alg. 1: path-traced radiance of samples
  * k0 .. k0+count-1 of each listed pixel at time t.
  *   pixels : device int32 [n_pix], values in [0, H*W) (may be NULL when n_pix = 0)

@@ -64,6 +64,11 @@ class Stats(C.Structure):
         return d
 
 
+class JobDesc(C.Structure):
+    _fields_ = [("ctx", C.c_void_p), ("t0", C.c_double), ("t1", C.c_double), ("events_out", C.c_void_p),
+                ("spp_out", C.c_void_p), ("mean_out", C.c_void_p)]
+
+
 class DetectArgs(C.Structure):
     _fields_ = [
         ("L", C.c_void_p), ("pixels", C.c_void_p), ("n_pix", C.c_int64), ("n_total", C.c_int64),
@@ -92,6 +97,8 @@ SIGNATURES = {
     "mcev_render_reference": (C.c_int, [C.c_void_p, C.c_double, C.c_int32]),
     "mcev_render_events": (C.c_int, [C.c_void_p, C.c_double, C.c_double, C.c_float, C.c_float, C.c_int32,
                                      C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(Stats)]),
+    "mcev_render_events_batch": (C.c_int, [C.c_void_p, C.POINTER(JobDesc), C.c_int32, C.c_float, C.c_float,
+                                           C.c_int32, C.c_int32, C.POINTER(Stats)]),
     "mcev_trace_samples": (C.c_int, [C.c_void_p, C.c_double, C.c_void_p, C.c_int64, C.c_int64, C.c_int32,
                                      C.c_void_p, C.c_void_p]),
     "mcev_state_bytes": (C.c_size_t, [C.c_void_p]),

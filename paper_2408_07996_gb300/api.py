@@ -207,3 +207,24 @@ class Renderer:
         mean = body[4 * n: 8 * n].view(torch.float32).view(self.height, self.width)
         m2 = body[8 * n: 12 * n].view(torch.float32).view(self.height, self.width)
         return cnt, mean, m2
+
+
+def render_events_batch(runner: Renderer, jobs, C_: float, alpha: float, spp_batch: int, spp_max: int,
+                        stats: bool = True):
+    """Batched Alg. 1 frames (include/mcev.h, mcev_render_events_batch).
+
+    jobs: list of (renderer, t0, t1); returns one dict of events / spp / mean
+    tensors per job, plus the runner's counters under "stats"."""
+    outs, descs = [], (L.JobDesc * len(jobs))()
+    for i, (r, t0, t1) in enumerate(jobs):
+        o = dict(events=torch.empty((r.height, r.width), dtype=torch.int8, device=r.device),
+                 spp=torch.empty((r.height, r.width), dtype=torch.int32, device=r.device),
+                 mean=torch.empty((r.height, r.width), dtype=torch.float32, device=r.device))
+        descs[i] = L.JobDesc(ctx=r.ctx, t0=float(t0), t1=float(t1), events_out=_tptr(o["events"]),
+                             spp_out=_tptr(o["spp"]), mean_out=_tptr(o["mean"]))
+        outs.append(o)
+    st = L.Stats()
+    L.check(runner.lib.mcev_render_events_batch(runner.ctx, descs, len(jobs), float(C_), float(alpha),
+                                                int(spp_batch), int(spp_max), C.byref(st) if stats else None),
+            runner.ctx, "mcev_render_events_batch")
+    return outs, (st.as_dict() if stats else None)

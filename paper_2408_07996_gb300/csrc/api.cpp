@@ -103,6 +103,9 @@ struct mcev_ctx {
     bool ref_valid = false;
     double ref_time = 0.0;
 
+    // batched renders run by this context: job table and union queues
+    DevBuf d_jobs, d_bqueue;
+
     // t critical values
     DevBuf d_tcrit;
     std::tuple<float, int, int, int, int> tcrit_key{-1.0f, -1, -1, -1, -1};
@@ -693,17 +696,33 @@ DevParams dev_params(const mcev_ctx* ctx, bool want_sig) {
     } while (0)
 
 // one chunk of n_paths = nj * spp_r paths through every bounce
+// Batched render (several contexts' frame pairs in one set of rounds): the
+// device job table, the union queues of (job << 24 | pixel) entries, and the
+// largest depth / any NEE over the jobs (the per-path kernels use each job's
+// own settings).
+struct BatchRun {
+    const Job* d_jobs = nullptr;
+    int32_t* queue[2] = {nullptr, nullptr};
+    int64_t q0 = 0;
+    int32_t max_depth = 0;
+    bool any_nee = false;
+};
+
+// one chunk of n_paths = nj * spp_r paths through every bounce
 mcev_status trace_chunk(mcev_ctx* ctx, const Frame& fr, const DevParams& P, const int32_t* queue, int64_t j0,
-                        int32_t spp_r, int64_t k_base, int64_t n_paths) {
+                        int32_t spp_r, int64_t k_base, int64_t n_paths, const BatchRun* B = nullptr) {
     const Wave& w = ctx->wave;
     int32_t* err = ctx->wave.counters + 15;
-    LAUNCH(MCEV_K_RAYGEN, launch_raygen(fr.dev, P, w, queue, j0, spp_r, k_base, n_paths, 0, ctx->sms, ctx->stream));
+    const Job* jobs = B ? B->d_jobs : nullptr;
+    const int depth_max = B ? B->max_depth : P.max_depth;
+    const bool nee = B ? B->any_nee : P.nee != 0;
+    LAUNCH(MCEV_K_RAYGEN, launch_raygen(fr.dev, P, w, queue, j0, spp_r, k_base, n_paths, 0, ctx->sms, ctx->stream, jobs));
     int cur = 0;
-    for (int depth = 0; depth <= P.max_depth; ++depth) {
-        LAUNCH(MCEV_K_EXTEND, launch_extend(ctx->dsc, fr.dev, P.t_min, w, cur, n_paths, err, ctx->sms, ctx->stream));
-        LAUNCH(MCEV_K_SHADE, launch_shade(ctx->dsc, fr.dev, P, w, cur, n_paths, ctx->sms, ctx->stream));
-        if (depth < P.max_depth && P.nee)
-            LAUNCH(MCEV_K_SHADOW, launch_shadow(ctx->dsc, fr.dev, P, w, n_paths, err, ctx->sms, ctx->stream));
+    for (int depth = 0; depth <= depth_max; ++depth) {
+        LAUNCH(MCEV_K_EXTEND, launch_extend(ctx->dsc, fr.dev, P.t_min, w, cur, n_paths, err, ctx->sms, ctx->stream, jobs));
+        LAUNCH(MCEV_K_SHADE, launch_shade(ctx->dsc, fr.dev, P, w, cur, n_paths, ctx->sms, ctx->stream, jobs));
+        if (depth < depth_max && nee)
+            LAUNCH(MCEV_K_SHADOW, launch_shadow(ctx->dsc, fr.dev, P, w, n_paths, err, ctx->sms, ctx->stream, jobs));
         cur ^= 1;
     }
     return MCEV_OK;
@@ -712,11 +731,21 @@ mcev_status trace_chunk(mcev_ctx* ctx, const Frame& fr, const DevParams& P, cons
 // Runs rounds of batches over the pixel queue until no pixel is undecided.
 // mode REFERENCE: every pixel to spp_max samples, statistics -> ref.
 // mode DETECT: Alg. 1 frame with the test variant in `A`.
-mcev_status run_rounds(mcev_ctx* ctx, const Frame& fr, StatsArgs A, int64_t* paths_out, int32_t* rounds_out) {
-    const int64_t npix = (int64_t)ctx->W * ctx->H;
+mcev_status run_rounds(mcev_ctx* ctx, const Frame& fr, StatsArgs A, int64_t* paths_out, int32_t* rounds_out,
+                       const BatchRun* B = nullptr) {
     const DevParams P = dev_params(ctx, false);
-    LAUNCH(MCEV_K_STATS, launch_iota(ctx->queue[0], npix, ctx->sms, ctx->stream));
-    int64_t Q = npix, n_done = 0, paths = 0;
+    int32_t* queue[2] = {ctx->queue[0], ctx->queue[1]};
+    int64_t Q;
+    if (B) {
+        queue[0] = B->queue[0];
+        queue[1] = B->queue[1];
+        Q = B->q0;
+    } else {
+        Q = (int64_t)ctx->W * ctx->H;
+        LAUNCH(MCEV_K_STATS, launch_iota(queue[0], Q, ctx->sms, ctx->stream));
+    }
+    const Job* jobs = B ? B->d_jobs : nullptr;
+    int64_t n_done = 0, paths = 0;
     int rounds = 0, qi = 0;
     int32_t h_count = 0;
     const int64_t window_max = ctx->params.batch_window > 0 ? ctx->params.batch_window : 16;
@@ -741,8 +770,8 @@ mcev_status run_rounds(mcev_ctx* ctx, const Frame& fr, StatsArgs A, int64_t* pat
         const int64_t per_chunk = std::max<int64_t>(1, ctx->wave.cap / spp_r);
         for (int64_t j0 = 0; j0 < Q; j0 += per_chunk) {
             const int64_t nj = std::min(per_chunk, Q - j0);
-            ST(trace_chunk(ctx, fr, P, ctx->queue[qi], j0, spp_r, n_done, nj * spp_r));
-            LAUNCH(MCEV_K_STATS, launch_stats(ctx->wave, A, ctx->queue[qi], j0, nj, ctx->queue[qi ^ 1], ctx->sms, ctx->stream));
+            ST(trace_chunk(ctx, fr, P, queue[qi], j0, spp_r, n_done, nj * spp_r, B));
+            LAUNCH(MCEV_K_STATS, launch_stats(ctx->wave, A, queue[qi], j0, nj, queue[qi ^ 1], ctx->sms, ctx->stream, jobs));
         }
         paths += Q * spp_r;
         n_done += spp_r;
@@ -769,6 +798,42 @@ void reset_call_counters(mcev_ctx* ctx) {
     }
     ctx->h2d = ctx->d2h = 0;
     ctx->evused = 0;
+}
+
+mcev_status fill_stats(mcev_ctx* ctx, mcev_stats* stats_out, int64_t paths, int64_t ref_paths, int32_t rounds) {
+    int32_t c[64];
+    CU(cudaMemcpyAsync(c, ctx->wave.counters, sizeof c, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    ctx->d2h += (int64_t)sizeof c;
+    float ms = 0.0f;
+    CU(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
+    uint64_t u[16];
+    std::memcpy(u, c + 32, sizeof u);
+    std::memset(stats_out, 0, sizeof *stats_out);
+    stats_out->paths = paths;
+    stats_out->samples_used = (int64_t)u[6];
+    stats_out->ref_paths = ref_paths;
+    stats_out->rounds = rounds;
+    stats_out->kernel_launches = ctx->launches;
+    stats_out->nonfinite = c[4];
+    stats_out->events_pos = c[5];
+    stats_out->events_neg = c[6];
+    stats_out->pixels_at_cap = c[7];
+    stats_out->gpu_ms = ms;
+    stats_out->nodes_closest = (int64_t)u[0];
+    stats_out->tris_closest = (int64_t)u[1];
+    stats_out->nodes_shadow = (int64_t)u[2];
+    stats_out->tris_shadow = (int64_t)u[3];
+    stats_out->rays_closest = (int64_t)u[4];
+    stats_out->rays_shadow = (int64_t)u[5];
+    for (int i = 0; i < MCEV_K_CLASSES; ++i) {
+        stats_out->kernel_count[i] = ctx->kcount[i];
+        stats_out->kernel_ms[i] = ctx->kms[i];
+    }
+    stats_out->h2d_bytes = ctx->h2d;
+    stats_out->d2h_bytes = ctx->d2h;
+    if (c[15]) return fail(ctx, MCEV_ERR_STATE, "traversal stack overflow");
+    return MCEV_OK;
 }
 
 mcev_status check_ready(mcev_ctx* ctx) {
@@ -844,7 +909,7 @@ void mcev_destroy(mcev_ctx* ctx) {
     cudaStreamSynchronize(ctx->stream);
     DevBuf* bufs[] = {&ctx->d_nodes, &ctx->d_tris, &ctx->d_mats, &ctx->d_env, &ctx->d_marg, &ctx->d_cond,
                       &ctx->d_tpdf, &ctx->frames[0].buf, &ctx->frames[1].buf, &ctx->d_wave, &ctx->d_counters,
-                      &ctx->d_pix, &ctx->d_tcrit};
+                      &ctx->d_pix, &ctx->d_tcrit, &ctx->d_jobs, &ctx->d_bqueue};
     for (DevBuf* b : bufs) dev_free(ctx, *b);
     for (cudaEvent_t e : ctx->evpool) cudaEventDestroy(e);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
@@ -1051,40 +1116,7 @@ mcev_status mcev_render_events(mcev_ctx* ctx, double t0, double t1, float C, flo
     ctx->ref_time = t1;
     CU(cudaEventRecord(ctx->ev1, ctx->stream));
     ST(drain_events(ctx));
-    if (stats_out) {
-        int32_t c[64];
-        CU(cudaMemcpyAsync(c, ctx->wave.counters, sizeof c, cudaMemcpyDeviceToHost, ctx->stream));
-        CU(cudaStreamSynchronize(ctx->stream));
-        ctx->d2h += (int64_t)sizeof c;
-        float ms = 0.0f;
-        CU(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
-        uint64_t u[16];
-        std::memcpy(u, c + 32, sizeof u);
-        std::memset(stats_out, 0, sizeof *stats_out);
-        stats_out->paths = paths;
-        stats_out->samples_used = (int64_t)u[6];
-        stats_out->ref_paths = ref_paths;
-        stats_out->rounds = rounds;
-        stats_out->kernel_launches = ctx->launches;
-        stats_out->nonfinite = c[4];
-        stats_out->events_pos = c[5];
-        stats_out->events_neg = c[6];
-        stats_out->pixels_at_cap = c[7];
-        stats_out->gpu_ms = ms;
-        stats_out->nodes_closest = (int64_t)u[0];
-        stats_out->tris_closest = (int64_t)u[1];
-        stats_out->nodes_shadow = (int64_t)u[2];
-        stats_out->tris_shadow = (int64_t)u[3];
-        stats_out->rays_closest = (int64_t)u[4];
-        stats_out->rays_shadow = (int64_t)u[5];
-        for (int i = 0; i < MCEV_K_CLASSES; ++i) {
-            stats_out->kernel_count[i] = ctx->kcount[i];
-            stats_out->kernel_ms[i] = ctx->kms[i];
-        }
-        stats_out->h2d_bytes = ctx->h2d;
-        stats_out->d2h_bytes = ctx->d2h;
-        if (c[15]) return fail(ctx, MCEV_ERR_STATE, "traversal stack overflow");
-    }
+    if (stats_out) ST(fill_stats(ctx, stats_out, paths, ref_paths, rounds));
     return MCEV_OK;
 }
 
@@ -1101,9 +1133,125 @@ mcev_status mcev_trace_samples(mcev_ctx* ctx, double t, const int32_t* pixels, i
     const int64_t per_chunk = std::max<int64_t>(1, ctx->wave.cap / count);
     for (int64_t j0 = 0; j0 < n_pix; j0 += per_chunk) {
         const int64_t nj = std::min(per_chunk, n_pix - j0);
-        ST(trace_chunk(ctx, ctx->frames[0], P, pixels, j0, count, k0, nj * count));
+        ST(trace_chunk(ctx, ctx->frames[0], P, pixels, j0, count, k0, nj * count, nullptr));
         LAUNCH(MCEV_K_STATS, launch_write_samples(ctx->wave, j0 * count, nj * count, L_out, sig_out, ctx->sms, ctx->stream));
     }
+    return MCEV_OK;
+}
+
+
+mcev_status mcev_render_events_batch(mcev_ctx* runner, const mcev_job* jobs, int32_t n_jobs, float C, float alpha,
+                                     int32_t spp_batch, int32_t spp_max, mcev_stats* stats_out) {
+    mcev_ctx* ctx = runner;
+    if (!ctx) return MCEV_ERR_ARG;
+    if (!jobs || n_jobs < 1 || n_jobs > 256) return fail(ctx, MCEV_ERR_ARG, "need 1..256 jobs");
+    if (!(C >= 0.0f) || !(alpha > 0.0f && alpha < 1.0f) || spp_batch < 1)
+        return fail(ctx, MCEV_ERR_ARG, "need C >= 0, 0 < alpha < 1, spp_batch >= 1");
+    const mcev_ctx* j0c = jobs[0].ctx;
+    if (!j0c) return fail(ctx, MCEV_ERR_ARG, "job 0 has no context");
+    const int32_t spp_min = j0c->params.spp_min, variant = j0c->params.variant, se_mode = j0c->params.se_mode;
+    if (spp_max < spp_min) return fail(ctx, MCEV_ERR_ARG, "spp_max < spp_min");
+    for (int i = 0; i < n_jobs; ++i) {
+        const mcev_ctx* c = jobs[i].ctx;
+        if (!c || !c->have_scene) return fail(ctx, MCEV_ERR_STATE, "job %d: no context or no scene", i);
+        if (c->device != ctx->device) return fail(ctx, MCEV_ERR_ARG, "job %d: context on another device", i);
+        if ((int64_t)c->W * c->H > (1 << 24)) return fail(ctx, MCEV_ERR_ARG, "job %d: more than 2^24 pixels", i);
+        if (!jobs[i].events_out) return fail(ctx, MCEV_ERR_ARG, "job %d: events_out is required", i);
+        if (c->params.spp_min != spp_min || c->params.variant != variant || c->params.se_mode != se_mode)
+            return fail(ctx, MCEV_ERR_ARG, "job %d: spp_min, variant and se_mode must match across jobs", i);
+        for (int k = 0; k < i; ++k)
+            if (jobs[k].ctx == c) return fail(ctx, MCEV_ERR_ARG, "jobs %d and %d share a context", k, i);
+    }
+    CU(cudaSetDevice(ctx->device));
+    ST(ensure_wave(ctx));
+    reset_call_counters(ctx);
+    CU(cudaStreamSynchronize(ctx->stream));
+    CU(cudaMemsetAsync(ctx->wave.counters + 4, 0, 60 * sizeof(int32_t), ctx->stream));
+    CU(cudaEventRecord(ctx->ev0, ctx->stream));
+    for (int i = 0; i < n_jobs; ++i) {
+        mcev_ctx* c = jobs[i].ctx;
+        ST(ensure_pixels(c));
+        CU(cudaStreamSynchronize(c->stream));
+    }
+    int64_t total = 0;
+    for (int i = 0; i < n_jobs; ++i) total += (int64_t)jobs[i].ctx->W * jobs[i].ctx->H;
+    ST(dev_alloc(ctx, ctx->d_bqueue, 2 * sizeof(int32_t) * (size_t)total));
+    ST(dev_alloc(ctx, ctx->d_jobs, sizeof(Job) * (size_t)n_jobs));
+    BatchRun B;
+    B.d_jobs = (const Job*)ctx->d_jobs.ptr;
+    B.queue[0] = (int32_t*)ctx->d_bqueue.ptr;
+    B.queue[1] = B.queue[0] + total;
+    // builds the job table of the listed jobs for frame slot `slot` and fills the queue
+    auto prepare = [&](const std::vector<int>& list, int slot) -> mcev_status {
+        std::vector<Job> tab(list.size());
+        B.q0 = 0;
+        B.max_depth = 0;
+        B.any_nee = false;
+        for (size_t q = 0; q < list.size(); ++q) {
+            mcev_ctx* c = jobs[list[q]].ctx;
+            Job& J = tab[q];
+            std::memset(&J, 0, sizeof J);
+            J.sc = c->dsc;
+            J.fr = c->frames[slot].dev;
+            J.P = dev_params(c, false);
+            J.cur = c->cur;
+            J.ref = c->ref;
+            J.events = jobs[list[q]].events_out;
+            J.spp_out = jobs[list[q]].spp_out;
+            J.mean_out = jobs[list[q]].mean_out;
+            B.max_depth = std::max(B.max_depth, c->params.max_depth);
+            B.any_nee = B.any_nee || c->params.nee != 0;
+            const int64_t np = (int64_t)c->W * c->H;
+            LAUNCH(MCEV_K_STATS, launch_fill_entries(B.queue[0] + B.q0, np, (int)q, ctx->sms, ctx->stream));
+            B.q0 += np;
+        }
+        CU(cudaMemcpyAsync(ctx->d_jobs.ptr, tab.data(), sizeof(Job) * tab.size(), cudaMemcpyHostToDevice, ctx->stream));
+        CU(cudaStreamSynchronize(ctx->stream));
+        ctx->h2d += (int64_t)(sizeof(Job) * tab.size());
+        return MCEV_OK;
+    };
+    // first frame of Alg. 1 for the jobs whose reference is not at t0
+    std::vector<int> need;
+    for (int i = 0; i < n_jobs; ++i)
+        if (!jobs[i].ctx->ref_valid || jobs[i].ctx->ref_time != jobs[i].t0) need.push_back(i);
+    int64_t ref_paths = 0, paths = 0;
+    int32_t rounds = 0;
+    if (!need.empty()) {
+        for (int i : need) ST(frame_setup(jobs[i].ctx, jobs[i].t0, 0));
+        ST(prepare(need, 0));
+        StatsArgs R{};
+        R.spp_min = R.spp_batch = R.spp_max = spp_max;
+        R.mode = MODE_REFERENCE;
+        ST(run_rounds(ctx, ctx->frames[0], R, &ref_paths, nullptr, &B));
+        for (int i : need) {
+            jobs[i].ctx->ref_valid = true;
+            jobs[i].ctx->ref_time = jobs[i].t0;
+        }
+    }
+    std::vector<int> all(n_jobs);
+    for (int i = 0; i < n_jobs; ++i) {
+        all[i] = i;
+        ST(frame_setup(jobs[i].ctx, jobs[i].t1, 1));
+    }
+    ST(prepare(all, 1));
+    ST(ensure_tcrit(ctx, alpha, variant, spp_min, spp_batch, spp_max));
+    StatsArgs A{};
+    A.tcrit = (const float*)ctx->d_tcrit.ptr;
+    A.C = C;
+    A.spp_min = spp_min;
+    A.spp_batch = spp_batch;
+    A.spp_max = spp_max;
+    A.mode = MODE_DETECT;
+    A.variant = variant;
+    A.se_mode = se_mode;
+    ST(run_rounds(ctx, ctx->frames[1], A, &paths, &rounds, &B));
+    for (int i = 0; i < n_jobs; ++i) {
+        jobs[i].ctx->ref_valid = true;
+        jobs[i].ctx->ref_time = jobs[i].t1;
+    }
+    CU(cudaEventRecord(ctx->ev1, ctx->stream));
+    ST(drain_events(ctx));
+    if (stats_out) ST(fill_stats(ctx, stats_out, paths, ref_paths, rounds));
     return MCEV_OK;
 }
 

@@ -38,8 +38,14 @@ static constexpr uint32_t NO_FLAGS = 0xFFFFFFFFu;
 static constexpr uint32_t FNV_BASIS = 2166136261u;
 
 // ------------------------------------------------------------------ raygen
+// kBatch: queue entries are (job << 24 | pixel) and every path reads its
+// job's frame and settings from the job table; otherwise entries are pixels
+// of the single context whose frame and settings are kernel arguments.  A
+// ray's `w` lane carries its bounce depth | job << 8.
+template <bool kBatch>
 __global__ void __launch_bounds__(256) k_raygen(DevFrame fr, DevParams P, Wave w, const int32_t* __restrict__ queue,
-                                                int64_t j0, int32_t spp_r, int64_t k_base, int64_t n_paths, int cur) {
+                                                int64_t j0, int32_t spp_r, int64_t k_base, int64_t n_paths, int cur,
+                                                const Job* __restrict__ jobs) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         w.counters[cur] = (int32_t)n_paths;
         w.counters[1 - cur] = 0;
@@ -48,22 +54,26 @@ __global__ void __launch_bounds__(256) k_raygen(DevFrame fr, DevParams P, Wave w
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n_paths; p += (int64_t)gridDim.x * blockDim.x) {
         const int64_t j = p / spp_r;
         const int32_t s = (int32_t)(p - j * spp_r);
-        const int32_t pix = __ldg(queue + j0 + j);
+        const int32_t entry = __ldg(queue + j0 + j);
+        const int job = kBatch ? (int)((uint32_t)entry >> 24) : 0;
+        const int32_t pix = kBatch ? (entry & 0xFFFFFF) : entry;
+        const DevFrame& F = kBatch ? jobs[job].fr : fr;
+        const DevParams& Q = kBatch ? jobs[job].P : P;
         const uint32_t k = (uint32_t)(k_base + s);
-        const uint4 x = philox4x32_10(make_uint4((uint32_t)pix, k, 0u, 0u), fr.key0, fr.key1);
-        const int px = pix % P.width, py = pix / P.width;
-        const float fx = 2.0f * ((float)px + u01(x.x)) / (float)P.width - 1.0f;
-        const float fy = 1.0f - 2.0f * ((float)py + u01(x.y)) / (float)P.height;
-        const f3 d = norm3(mk3(fr.fwd[0] + fx * fr.right[0] + fy * fr.up[0],
-                               fr.fwd[1] + fx * fr.right[1] + fy * fr.up[1],
-                               fr.fwd[2] + fx * fr.right[2] + fy * fr.up[2]));
-        w.ray_o[cur][p] = make_float4(fr.eye[0], fr.eye[1], fr.eye[2], __int_as_float((int)p));
-        w.ray_d[cur][p] = make_float4(d.x, d.y, d.z, __int_as_float(0));
+        const uint4 x = philox4x32_10(make_uint4((uint32_t)pix, k, 0u, 0u), F.key0, F.key1);
+        const int px = pix % Q.width, py = pix / Q.width;
+        const float fx = 2.0f * ((float)px + u01(x.x)) / (float)Q.width - 1.0f;
+        const float fy = 1.0f - 2.0f * ((float)py + u01(x.y)) / (float)Q.height;
+        const f3 d = norm3(mk3(F.fwd[0] + fx * F.right[0] + fy * F.up[0],
+                               F.fwd[1] + fx * F.right[1] + fy * F.up[1],
+                               F.fwd[2] + fx * F.right[2] + fy * F.up[2]));
+        w.ray_o[cur][p] = make_float4(F.eye[0], F.eye[1], F.eye[2], __int_as_float((int)p));
+        w.ray_d[cur][p] = make_float4(d.x, d.y, d.z, __int_as_float(job << 8));
         w.beta[p] = 1.0f;
         w.L[p] = 0.0f;
         w.pdf_prev[p] = 0.0f;
-        w.pix_k[p] = make_int2(pix, (int)k);
-        if (P.want_sig) {
+        w.pix_k[p] = make_int2(entry, (int)k);
+        if (Q.want_sig) {
             w.sig[p] = FNV_BASIS;
             w.pflags[p] = NO_FLAGS;
         }
@@ -84,7 +94,9 @@ __device__ __forceinline__ void add_work(const Wave& w, int which, int2 work) {
 }
 
 // ------------------------------------------------------------------ extend
-__global__ void MCEV_TRAV_BOUNDS k_extend(DevScene sc, DevFrame fr, float t_min, Wave w, int cur, int32_t* err) {
+template <bool kBatch>
+__global__ void MCEV_TRAV_BOUNDS k_extend(DevScene sc, DevFrame fr, float t_min, Wave w, int cur, int32_t* err,
+                                          const Job* __restrict__ jobs) {
     const int32_t n = *(volatile int32_t*)(w.counters + cur);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         w.counters[1 - cur] = 0;
@@ -96,7 +108,11 @@ __global__ void MCEV_TRAV_BOUNDS k_extend(DevScene sc, DevFrame fr, float t_min,
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const float4 o = w.ray_o[cur][i];
         const float4 d = w.ray_d[cur][i];
-        const Hit h = closest_hit(sc, fr, xyz(o), xyz(d), t_min, &e, work);
+        const int job = kBatch ? (__float_as_int(d.w) >> 8) : 0;
+        const DevScene& S = kBatch ? jobs[job].sc : sc;
+        const DevFrame& F = kBatch ? jobs[job].fr : fr;
+        const float tmin = kBatch ? jobs[job].P.t_min : t_min;
+        const Hit h = closest_hit(S, F, xyz(o), xyz(d), tmin, &e, work);
         w.hit[i] = make_float4(h.t, __int_as_float(h.inst), __int_as_float(h.tri), __int_as_float(h.rec));
     }
     if (e) atomicOr(err, 1);
@@ -114,20 +130,26 @@ __global__ void MCEV_TRAV_BOUNDS k_extend(DevScene sc, DevFrame fr, float t_min,
 #else
 #define MCEV_SHADE_BOUNDS __launch_bounds__(128)
 #endif
-__global__ void MCEV_SHADE_BOUNDS k_shade(DevScene sc, DevFrame fr, DevParams P, Wave w, int cur) {
+template <bool kBatch>
+__global__ void MCEV_SHADE_BOUNDS k_shade(DevScene sc, DevFrame fr, DevParams P, Wave w, int cur,
+                                          const Job* __restrict__ jobs) {
     const int32_t n = *(volatile int32_t*)(w.counters + cur);
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const float4 ro = w.ray_o[cur][i];
         const float4 rd = w.ray_d[cur][i];
         const int p = __float_as_int(ro.w);
-        const int depth = __float_as_int(rd.w);
+        const int depth = __float_as_int(rd.w) & 0xFF;
+        const int job = kBatch ? (__float_as_int(rd.w) >> 8) : 0;
+        const DevScene& S = kBatch ? jobs[job].sc : sc;
+        const DevFrame& F = kBatch ? jobs[job].fr : fr;
+        const DevParams& Q = kBatch ? jobs[job].P : P;
         const float4 hv = w.hit[i];
         const int inst = __float_as_int(hv.y);
         float beta = w.beta[p];
         float L = w.L[p];
         const float pdf_prev = w.pdf_prev[p];
         uint32_t sig = 0, pflags = NO_FLAGS;
-        if (P.want_sig) {
+        if (Q.want_sig) {
             sig = w.sig[p];
             const uint32_t pf = w.pflags[p];
             if (pf != NO_FLAGS) sig = fnv(sig, pf);
@@ -138,28 +160,28 @@ __global__ void MCEV_SHADE_BOUNDS k_shade(DevScene sc, DevFrame fr, DevParams P,
         float sh_tmax = 0.0f, sh_c = 0.0f;
         if (inst < 0) {
             // miss: environment radiance (Sec. 3.1 samples the light reaching the pixel)
-            if (P.want_sig) sig = fnv(sig, 0xFFFFFFFFu);
-            if (sc.has_env) {
+            if (Q.want_sig) sig = fnv(sig, 0xFFFFFFFFu);
+            if (S.has_env) {
                 int row, col;
                 float st;
-                env_texel(sc, d, row, col, st);
-                if (P.want_sig) sig = fnv(sig, (uint32_t)(row * sc.env_w + col));
-                const float Le = __ldg(sc.env + (int64_t)row * sc.env_w + col);
+                env_texel(S, d, row, col, st);
+                if (Q.want_sig) sig = fnv(sig, (uint32_t)(row * S.env_w + col));
+                const float Le = __ldg(S.env + (int64_t)row * S.env_w + col);
                 float wgt = 1.0f;
-                if (depth > 0 && P.nee) wgt = P.mis ? power_heuristic(pdf_prev, fr.p_env * texel_pdf(sc, row, col, st)) : 0.0f;
+                if (depth > 0 && Q.nee) wgt = Q.mis ? power_heuristic(pdf_prev, F.p_env * texel_pdf(S, row, col, st)) : 0.0f;
                 L += beta * wgt * Le;
-            } else if (P.want_sig) {
+            } else if (Q.want_sig) {
                 sig = fnv(sig, 0xFFFFFFFEu);
             }
         } else {
             const int tri = __float_as_int(hv.z);
-            const float4* tp = sc.tris + 3 * tri;
+            const float4* tp = S.tris + 3 * tri;
             const float4 q0 = __ldg(tp), q1 = __ldg(tp + 1), q2 = __ldg(tp + 2);
-            const float4* ip = fr.inst + 7 * __float_as_int(hv.w);
+            const float4* ip = F.inst + 7 * __float_as_int(hv.w);
             const float4 m0 = __ldg(ip), m1 = __ldg(ip + 1), m2 = __ldg(ip + 2);
             const float4 i0 = __ldg(ip + 3), i1 = __ldg(ip + 4), i2 = __ldg(ip + 5);
             const int ovr = __float_as_int(__ldg(ip + 6).y);
-            if (P.want_sig) {
+            if (Q.want_sig) {
                 sig = fnv(sig, (uint32_t)inst);
                 sig = fnv(sig, (uint32_t)__float_as_int(q0.w));
             }
@@ -170,7 +192,7 @@ __global__ void MCEV_SHADE_BOUNDS k_shade(DevScene sc, DevFrame fr, DevParams P,
             const f3 ng = norm3(xf_normal(i0, i1, i2, cr));
             const f3 wo = d * -1.0f;
             const int mat = ovr >= 0 ? ovr : __float_as_int(q1.w);
-            const float4 mv = __ldg(sc.mats + mat);
+            const float4 mv = __ldg(S.mats + mat);
             const int type = __float_as_int(mv.x);
             const float alb = mv.y, rough = mv.z, emit = mv.w;
             uint32_t flags = 0;
@@ -178,52 +200,53 @@ __global__ void MCEV_SHADE_BOUNDS k_shade(DevScene sc, DevFrame fr, DevParams P,
             if (emit > 0.0f && cos_o > 0.0f) {
                 flags |= 1u;
                 float wgt = 1.0f;
-                if (depth > 0 && P.nee) {
-                    if (!P.mis) {
+                if (depth > 0 && Q.nee) {
+                    if (!Q.mis) {
                         wgt = 0.0f;
                     } else {
                         const f3 we1 = xf_vec(m0, m1, m2, e1), we2 = xf_vec(m0, m1, m2, e2);
                         const f3 wc = cross3(we1, we2);
                         const float area = 0.5f * sqrtf(dot3(wc, wc));
-                        const float pl = fr.p_area / ((float)fr.n_lights * area) * t * t / cos_o;
+                        const float pl = F.p_area / ((float)F.n_lights * area) * t * t / cos_o;
                         wgt = power_heuristic(pdf_prev, pl);
                     }
                 }
                 L += beta * wgt * emit;
             }
-            if (depth < P.max_depth && alb > 0.0f) {
+            if (depth < Q.max_depth && alb > 0.0f) {
                 const f3 nn = cos_o < 0.0f ? ng * -1.0f : ng;
                 f3 tb, bt;
                 onb(nn, tb, bt);
                 const f3 wol = mk3(dot3(wo, tb), dot3(wo, bt), dot3(wo, nn));
-                const uint2 pk = make_uint2((uint32_t)w.pix_k[p].x, (uint32_t)w.pix_k[p].y);
+                const int2 pkv = w.pix_k[p];
+                const uint2 pk = make_uint2(kBatch ? ((uint32_t)pkv.x & 0xFFFFFFu) : (uint32_t)pkv.x, (uint32_t)pkv.y);
                 // next-event estimation
-                if (P.nee && (sc.env_ok || fr.n_lights > 0)) {
-                    const uint4 x = philox4x32_10(make_uint4(pk.x, pk.y, (uint32_t)(depth + 1), 0u), fr.key0, fr.key1);
-                    const bool use_env = sc.env_ok && (fr.n_lights == 0 || u01(x.x) < 0.5f);
+                if (Q.nee && (S.env_ok || F.n_lights > 0)) {
+                    const uint4 x = philox4x32_10(make_uint4(pk.x, pk.y, (uint32_t)(depth + 1), 0u), F.key0, F.key1);
+                    const bool use_env = S.env_ok && (F.n_lights == 0 || u01(x.x) < 0.5f);
                     f3 wi = mk3(0, 0, 0);
                     float pl = 0.0f, Le = 0.0f, tmax = __int_as_float(0x7f800000);
                     if (use_env) {
                         float pdf;
-                        wi = env_sample(sc, u01(x.z), u01(x.w), pdf, Le);
-                        pl = fr.p_env * pdf;
+                        wi = env_sample(S, u01(x.z), u01(x.w), pdf, Le);
+                        pl = F.p_env * pdf;
                     } else {
                         const uint64_t mm = (uint64_t)(x.y >> 8);
-                        const int li = (int)((mm * (uint64_t)fr.n_lights) >> 24);
-                        const float4* lp = fr.lights + 4 * li;
+                        const int li = (int)((mm * (uint64_t)F.n_lights) >> 24);
+                        const float4* lp = F.lights + 4 * li;
                         const float4 a0 = __ldg(lp), a1 = __ldg(lp + 1), a2 = __ldg(lp + 2), an = __ldg(lp + 3);
                         const float su = sqrtf(u01(x.z));
                         const float b0 = 1.0f - su, b1 = u01(x.w) * su, b2 = 1.0f - b0 - b1;
-                        const f3 Q = xyz(a0) * b0 + xyz(a1) * b1 + xyz(a2) * b2;
-                        const f3 dv = Q - P0;
+                        const f3 Ql = xyz(a0) * b0 + xyz(a1) * b1 + xyz(a2) * b2;
+                        const f3 dv = Ql - P0;
                         const float dist = sqrtf(dot3(dv, dv));
                         wi = dv * (1.0f / dist);
                         const float cl = -dot3(xyz(an), wi);
                         if (cl > 0.0f) {
-                            pl = fr.p_area / ((float)fr.n_lights * a1.w) * dist * dist / cl;
+                            pl = F.p_area / ((float)F.n_lights * a1.w) * dist * dist / cl;
                             Le = a0.w;
                         }
-                        tmax = dist - P.t_min;
+                        tmax = dist - Q.t_min;
                     }
                     if (pl > 0.0f && Le > 0.0f) {
                         const f3 wil = mk3(dot3(wi, tb), dot3(wi, bt), dot3(wi, nn));
@@ -231,7 +254,7 @@ __global__ void MCEV_SHADE_BOUNDS k_shade(DevScene sc, DevFrame fr, DevParams P,
                         const float f = bsdf_eval(type, alb, rough, wol, wil, &pb);
                         if (f > 0.0f && wil.z > 0.0f) {
                             flags |= 2u;
-                            const float wgt = P.mis ? power_heuristic(pl, pb) : 1.0f;
+                            const float wgt = Q.mis ? power_heuristic(pl, pb) : 1.0f;
                             sh_c = beta * f * wil.z * Le * wgt / pl;
                             sh_dir = wi;
                             sh_tmax = tmax;
@@ -240,7 +263,7 @@ __global__ void MCEV_SHADE_BOUNDS k_shade(DevScene sc, DevFrame fr, DevParams P,
                     }
                 }
                 // BSDF sampling of the continuation
-                const uint4 y = philox4x32_10(make_uint4(pk.x, pk.y, (uint32_t)(depth + 1), 1u), fr.key0, fr.key1);
+                const uint4 y = philox4x32_10(make_uint4(pk.x, pk.y, (uint32_t)(depth + 1), 1u), F.key0, F.key1);
                 const f3 wil = bsdf_sample(type, rough, wol, u01(y.x), u01(y.y));
                 float pb;
                 const float f = bsdf_eval(type, alb, rough, wol, wil, &pb);
@@ -256,7 +279,7 @@ __global__ void MCEV_SHADE_BOUNDS k_shade(DevScene sc, DevFrame fr, DevParams P,
         }
         w.L[p] = L;
         w.beta[p] = beta;
-        if (P.want_sig) {
+        if (Q.want_sig) {
             w.sig[p] = sig;
             w.pflags[p] = pflags;
         }
@@ -269,13 +292,15 @@ __global__ void MCEV_SHADE_BOUNDS k_shade(DevScene sc, DevFrame fr, DevParams P,
         const int ni = warp_append(w.counters + (1 - cur), cont);
         if (cont) {
             w.ray_o[1 - cur][ni] = make_float4(P0.x, P0.y, P0.z, __int_as_float(p));
-            w.ray_d[1 - cur][ni] = make_float4(wi_next.x, wi_next.y, wi_next.z, __int_as_float(depth + 1));
+            w.ray_d[1 - cur][ni] = make_float4(wi_next.x, wi_next.y, wi_next.z, __int_as_float((depth + 1) | (job << 8)));
         }
     }
 }
 
 // ------------------------------------------------------------------ shadow rays
-__global__ void MCEV_TRAV_BOUNDS k_shadow(DevScene sc, DevFrame fr, DevParams P, Wave w, int32_t* err) {
+template <bool kBatch>
+__global__ void MCEV_TRAV_BOUNDS k_shadow(DevScene sc, DevFrame fr, DevParams P, Wave w, int32_t* err,
+                                          const Job* __restrict__ jobs) {
     const int32_t n = *(volatile int32_t*)(w.counters + 2);
     if (blockIdx.x == 0 && threadIdx.x == 0)
         atomicAdd(reinterpret_cast<unsigned long long*>(w.counters + 32) + 5, (unsigned long long)n);
@@ -285,9 +310,13 @@ __global__ void MCEV_TRAV_BOUNDS k_shadow(DevScene sc, DevFrame fr, DevParams P,
         const float4 o = w.sh_o[i];
         const float4 d = w.sh_d[i];
         const int p = __float_as_int(o.w);
-        if (!occluded(sc, fr, xyz(o), xyz(d), P.t_min, d.w, &e, work)) {
+        const int job = kBatch ? (int)((uint32_t)w.pix_k[p].x >> 24) : 0;
+        const DevScene& S = kBatch ? jobs[job].sc : sc;
+        const DevFrame& F = kBatch ? jobs[job].fr : fr;
+        const DevParams& Q = kBatch ? jobs[job].P : P;
+        if (!occluded(S, F, xyz(o), xyz(d), Q.t_min, d.w, &e, work)) {
             w.L[p] += w.sh_c[i];
-            if (P.want_sig) w.pflags[p] |= 4u;
+            if (Q.want_sig) w.pflags[p] |= 4u;
         }
     }
     if (e) atomicOr(err, 1);
@@ -313,14 +342,27 @@ __device__ __forceinline__ Moments chan(Moments a, Moments b) {
 
 // kChecked: caller-supplied pixel ids and counts are range-checked (the
 // allocation-free entry point); the renderer's own queues use <false>.
-template <bool kChecked>
-__global__ void __launch_bounds__(256) k_stats(Wave w, StatsArgs A, const int32_t* __restrict__ queue, int64_t j0,
-                                               int64_t n_pix, int32_t* __restrict__ next_queue) {
+template <bool kChecked, bool kBatch>
+__global__ void __launch_bounds__(256) k_stats(Wave w, StatsArgs A0, const int32_t* __restrict__ queue, int64_t j0,
+                                               int64_t n_pix, int32_t* __restrict__ next_queue,
+                                               const Job* __restrict__ jobs) {
     const int lane = threadIdx.x & 31;
     const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t j = warp0; j < n_pix; j += nwarps) {
-        const int32_t pix = __ldg(queue + j0 + j);
+        const int32_t entry = __ldg(queue + j0 + j);
+        const int32_t pix = kBatch ? (entry & 0xFFFFFF) : entry;
+        // per-pixel state and outputs of the pixel's job
+        StatsArgs A = A0;
+        if (kBatch) {
+            const Job& J = jobs[(uint32_t)entry >> 24];
+            A.cur = J.cur;
+            A.ref = J.ref;
+            A.events = J.events;
+            A.spp_out = J.spp_out;
+            A.mean_out = J.mean_out;
+            A.eps = J.P.eps;
+        }
         if (kChecked && (pix < 0 || (int64_t)pix >= A.n_total)) {
             if (lane == 0) atomicOr(w.counters + 8, 1);
             continue;
@@ -403,12 +445,12 @@ __global__ void __launch_bounds__(256) k_stats(Wave w, StatsArgs A, const int32_
                 A.ref.mean[pix] = c.mean;
                 A.ref.m2[pix] = c.m2;
             } else {
-                next_queue[atomicAdd(w.counters + 3, 1)] = pix;
+                next_queue[atomicAdd(w.counters + 3, 1)] = entry;
             }
             continue;
         }
         if (!decided) {
-            next_queue[atomicAdd(w.counters + 3, 1)] = pix;
+            next_queue[atomicAdd(w.counters + 3, 1)] = entry;
             continue;
         }
         const float delta = c.mean - ma;
@@ -457,38 +499,73 @@ static int grid_for(int64_t work, int block, int sms, int per_sm) {
 }
 
 cudaError_t launch_raygen(const DevFrame& fr, const DevParams& P, const Wave& w, const int32_t* queue, int64_t j0,
-                          int32_t spp_r, int64_t k_base, int64_t n_paths, int cur, int sms, cudaStream_t st) {
-    k_raygen<<<grid_for(n_paths, 256, sms, 16), 256, 0, st>>>(fr, P, w, queue, j0, spp_r, k_base, n_paths, cur);
+                          int32_t spp_r, int64_t k_base, int64_t n_paths, int cur, int sms, cudaStream_t st,
+                          const Job* jobs) {
+    if (jobs)
+        k_raygen<true><<<grid_for(n_paths, 256, sms, 16), 256, 0, st>>>(fr, P, w, queue, j0, spp_r, k_base, n_paths,
+                                                                          cur, jobs);
+    else
+        k_raygen<false><<<grid_for(n_paths, 256, sms, 16), 256, 0, st>>>(fr, P, w, queue, j0, spp_r, k_base, n_paths,
+                                                                           cur, nullptr);
     return cudaGetLastError();
 }
 
 cudaError_t launch_extend(const DevScene& sc, const DevFrame& fr, float t_min, const Wave& w, int cur, int64_t max_n,
-                          int32_t* err, int sms, cudaStream_t st) {
-    k_extend<<<grid_for(max_n, MCEV_TRAV_BLOCK, sms, 16), MCEV_TRAV_BLOCK, 0, st>>>(sc, fr, t_min, w, cur, err);
+                          int32_t* err, int sms, cudaStream_t st, const Job* jobs) {
+    if (jobs)
+        k_extend<true><<<grid_for(max_n, MCEV_TRAV_BLOCK, sms, 16), MCEV_TRAV_BLOCK, 0, st>>>(sc, fr, t_min, w, cur,
+                                                                                              err, jobs);
+    else
+        k_extend<false><<<grid_for(max_n, MCEV_TRAV_BLOCK, sms, 16), MCEV_TRAV_BLOCK, 0, st>>>(sc, fr, t_min, w, cur,
+                                                                                               err, nullptr);
     return cudaGetLastError();
 }
 
 cudaError_t launch_shade(const DevScene& sc, const DevFrame& fr, const DevParams& P, const Wave& w, int cur,
-                         int64_t max_n, int sms, cudaStream_t st) {
-    k_shade<<<grid_for(max_n, 128, sms, 16), 128, 0, st>>>(sc, fr, P, w, cur);
+                         int64_t max_n, int sms, cudaStream_t st, const Job* jobs) {
+    if (jobs)
+        k_shade<true><<<grid_for(max_n, 128, sms, 16), 128, 0, st>>>(sc, fr, P, w, cur, jobs);
+    else
+        k_shade<false><<<grid_for(max_n, 128, sms, 16), 128, 0, st>>>(sc, fr, P, w, cur, nullptr);
     return cudaGetLastError();
 }
 
 cudaError_t launch_shadow(const DevScene& sc, const DevFrame& fr, const DevParams& P, const Wave& w, int64_t max_n,
-                          int32_t* err, int sms, cudaStream_t st) {
-    k_shadow<<<grid_for(max_n, MCEV_TRAV_BLOCK, sms, 16), MCEV_TRAV_BLOCK, 0, st>>>(sc, fr, P, w, err);
+                          int32_t* err, int sms, cudaStream_t st, const Job* jobs) {
+    if (jobs)
+        k_shadow<true><<<grid_for(max_n, MCEV_TRAV_BLOCK, sms, 16), MCEV_TRAV_BLOCK, 0, st>>>(sc, fr, P, w, err, jobs);
+    else
+        k_shadow<false><<<grid_for(max_n, MCEV_TRAV_BLOCK, sms, 16), MCEV_TRAV_BLOCK, 0, st>>>(sc, fr, P, w, err,
+                                                                                               nullptr);
     return cudaGetLastError();
 }
 
 cudaError_t launch_stats(const Wave& w, const StatsArgs& A, const int32_t* queue, int64_t j0, int64_t n_pix,
-                         int32_t* next_queue, int sms, cudaStream_t st) {
-    k_stats<false><<<grid_for(n_pix * 32, 256, sms, 8), 256, 0, st>>>(w, A, queue, j0, n_pix, next_queue);
+                         int32_t* next_queue, int sms, cudaStream_t st, const Job* jobs) {
+    if (jobs)
+        k_stats<false, true><<<grid_for(n_pix * 32, 256, sms, 8), 256, 0, st>>>(w, A, queue, j0, n_pix, next_queue,
+                                                                                 jobs);
+    else
+        k_stats<false, false><<<grid_for(n_pix * 32, 256, sms, 8), 256, 0, st>>>(w, A, queue, j0, n_pix, next_queue,
+                                                                                  nullptr);
     return cudaGetLastError();
 }
 
 static cudaError_t launch_stats_checked(const Wave& w, const StatsArgs& A, const int32_t* queue, int64_t n_pix,
                                         int32_t* next_queue, int sms, cudaStream_t st) {
-    k_stats<true><<<grid_for(n_pix * 32, 256, sms, 8), 256, 0, st>>>(w, A, queue, 0, n_pix, next_queue);
+    k_stats<true, false><<<grid_for(n_pix * 32, 256, sms, 8), 256, 0, st>>>(w, A, queue, 0, n_pix, next_queue,
+                                                                             nullptr);
+    return cudaGetLastError();
+}
+
+// queue entries (job << 24 | pixel) of one job
+__global__ void k_fill_entries(int32_t* q, int64_t n, int job) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        q[i] = (int32_t)(((uint32_t)job << 24) | (uint32_t)i);
+}
+
+cudaError_t launch_fill_entries(int32_t* q, int64_t n, int job, int sms, cudaStream_t st) {
+    k_fill_entries<<<grid_for(n, 256, sms, 8), 256, 0, st>>>(q, n, job);
     return cudaGetLastError();
 }
 

@@ -26,16 +26,20 @@ struct StatsArgs {
     int64_t n_total;      // per-pixel array length, checked only by the allocation-free entry point
 };
 
+// `jobs`: device job table of a batched render, or nullptr for a single
+// context (then the frame / settings / state arguments are used)
 cudaError_t launch_raygen(const DevFrame& fr, const DevParams& P, const Wave& w, const int32_t* queue, int64_t j0,
-                          int32_t spp_r, int64_t k_base, int64_t n_paths, int cur, int sms, cudaStream_t st);
+                          int32_t spp_r, int64_t k_base, int64_t n_paths, int cur, int sms, cudaStream_t st,
+                          const Job* jobs);
 cudaError_t launch_extend(const DevScene& sc, const DevFrame& fr, float t_min, const Wave& w, int cur, int64_t max_n,
-                          int32_t* err, int sms, cudaStream_t st);
+                          int32_t* err, int sms, cudaStream_t st, const Job* jobs);
 cudaError_t launch_shade(const DevScene& sc, const DevFrame& fr, const DevParams& P, const Wave& w, int cur,
-                         int64_t max_n, int sms, cudaStream_t st);
+                         int64_t max_n, int sms, cudaStream_t st, const Job* jobs);
 cudaError_t launch_shadow(const DevScene& sc, const DevFrame& fr, const DevParams& P, const Wave& w, int64_t max_n,
-                          int32_t* err, int sms, cudaStream_t st);
+                          int32_t* err, int sms, cudaStream_t st, const Job* jobs);
 cudaError_t launch_stats(const Wave& w, const StatsArgs& A, const int32_t* queue, int64_t j0, int64_t n_pix,
-                         int32_t* next_queue, int sms, cudaStream_t st);
+                         int32_t* next_queue, int sms, cudaStream_t st, const Job* jobs);
+cudaError_t launch_fill_entries(int32_t* q, int64_t n, int job, int sms, cudaStream_t st);
 cudaError_t launch_write_samples(const Wave& w, int64_t out0, int64_t n_paths, float* L_out, uint32_t* sig_out,
                                  int sms, cudaStream_t st);
 cudaError_t launch_iota(int32_t* q, int64_t n, int sms, cudaStream_t st);

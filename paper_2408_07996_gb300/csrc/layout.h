@@ -111,4 +111,17 @@ struct PixStats {
     float* m2;
 };
 
+// One frame pair of a batched render: its context's scene, frame, render
+// settings, per-pixel state and outputs.  Batched queue entries are
+// (job << 24 | pixel).
+struct Job {
+    DevScene sc;
+    DevFrame fr;
+    DevParams P;
+    PixStats cur, ref;
+    int8_t* events;
+    int32_t* spp_out;
+    float* mean_out;
+};
+
 }  // namespace mcev

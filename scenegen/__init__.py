@@ -10,6 +10,8 @@ from .procedural import (  # noqa: F401
     Scene,
     Workload,
     WORKLOADS,
+    BATCH_RESOLUTIONS,
+    batch_workloads,
     cornell_box,
     empty_env,
     furnace_sphere,

@@ -522,3 +522,32 @@ def workload(name: str, **over) -> Workload:
 
 
 WORKLOADS = ("cornell64", "spheres512", "terrain720p")
+
+BATCH_RESOLUTIONS = ((128, 128), (320, 240), (346, 260), (640, 480))
+
+
+def batch_workloads(n_jobs: int = 64, seed: int = 20240818) -> list:
+    """Independent frame-pair jobs for batched rendering (config 4): image
+    sizes drawn uniformly from BATCH_RESOLUTIONS, scenes of 5k-100k
+    triangles (displaced icosphere fields of 1-19 level-4 spheres, or 4-78
+    level-3 spheres, each with one spinning sphere and a moving camera),
+    schedule spp 16 -> +16 -> 4096, C = 0.2, alpha = 0.05."""
+    rng = np.random.default_rng(seed)
+    jobs = []
+    for j in range(n_jobs):
+        W, H = BATCH_RESOLUTIONS[int(rng.integers(len(BATCH_RESOLUTIONS)))]
+        target = int(rng.uniform(5_000, 100_000))
+        level = int(rng.integers(3, 5))
+        per = 20 * 4 ** level
+        n_sph = int(max(1, min(target // per, 19 if level == 4 else 78)))
+        sc = icosphere_field(seed + 1000 + j, n_spheres=n_sph, level=level, n_frames=9, dt=2.0e-3,
+                             env_w=128, env_h=64)
+        k = len(sc.key_times)
+        shift = np.linspace(0.0, 0.08, k)[:, None] * np.array([1.0, 0.0, 0.0])
+        sc.cam_eye = sc.cam_eye + shift
+        sc.cam_target = sc.cam_target + shift
+        w = Workload(f"batch{j}", sc, W, H, list(sc.key_times), spp_min=16, spp_batch=16, spp_max=4096,
+                     C=0.2, alpha=0.05, max_depth=4, seed=seed + j)
+        w.t_min = 1e-4 * _bbox_diag(sc)
+        jobs.append(w)
+    return jobs

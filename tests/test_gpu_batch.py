@@ -1,0 +1,125 @@
+"""Batched rendering (many frame pairs of different scenes and image sizes
+in shared rounds) against rendering every job on its own: identical events,
+sample counts and means, frame after frame, and against the oracle on the
+smallest job."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import scenegen as sg
+from paper_2408_07996_gb300.api import Renderer, render_events_batch
+
+pytestmark = pytest.mark.gpu
+
+SCHEDULE = dict(C=0.2, alpha=0.05, spp_batch=16, spp_max=256)
+SCHED = tuple(SCHEDULE.values())    # positional: (C, alpha, spp_batch, spp_max)
+
+
+def _jobs():
+    c = sg.workload("cornell64")
+    small = sg.icosphere_field(7, n_spheres=6, level=3, n_frames=3, dt=5e-3, env_w=64, env_h=32)
+    ws = [
+        (c.scene, 64, 64, c),
+        (c.scene, 40, 24, c),
+        (small, 96, 64, None),
+        (sg.empty_env(2.0), 16, 16, None),
+    ]
+    out = []
+    for sc, W, H, base in ws:
+        w = sg.Workload("job", sc, W, H, [0.0, 1.0, 2.0], spp_min=16, spp_batch=16, spp_max=256, C=0.2,
+                        alpha=0.05, max_depth=4, seed=99 + W, t_min=2e-4 if base is None else base.t_min)
+        out.append(w)
+    return out
+
+
+def _renderers(ws):
+    rs = []
+    for w in ws:
+        r = Renderer(w.width, w.height)
+        r.upload(w.scene)
+        r.configure(w)
+        rs.append(r)
+    return rs
+
+
+@pytest.mark.parametrize("runner_is_job", [False, True])
+def test_batch_equals_single(runner_is_job):
+    ws = _jobs()
+    frames = [(0.0, 1.0), (1.0, 2.0)]
+    single = _renderers(ws)
+    expect = []
+    for f in frames:
+        expect.append([{k: v.clone() for k, v in r.render_events(*f, *SCHED).items() if k != "stats"}
+                       for r in single])
+    for r in single:
+        r.close()
+    batch = _renderers(ws)
+    runner = batch[0] if runner_is_job else Renderer(8, 8)
+    for fi, f in enumerate(frames):
+        outs, st = render_events_batch(runner, [(r, f[0], f[1]) for r in batch], *SCHED)
+        if fi == 0:
+            assert st["ref_paths"] == sum(w.width * w.height for w in ws) * SCHEDULE["spp_max"]
+        else:
+            assert st["ref_paths"] == 0
+        assert st["samples_used"] == sum(int(o["spp"].sum()) for o in outs)
+        for j, (o, e) in enumerate(zip(outs, expect[fi])):
+            for k in ("events", "spp", "mean"):
+                assert torch.equal(o[k], e[k]), (fi, j, k)
+    for r in batch:
+        r.close()
+    if not runner_is_job:
+        runner.close()
+
+
+def test_batch_job_matches_oracle():
+    ws = _jobs()[1:2]            # the 40x24 Cornell job
+    w = ws[0]
+    r = _renderers(ws)[0]
+    runner = Renderer(8, 8)
+    outs, _ = render_events_batch(runner, [(r, 0.0, 1.0)], *SCHED)
+    osc = O.OracleScene(w.scene)
+    pix = np.arange(w.width * w.height, dtype=np.int32)
+    ref = O.render_events(osc, O.params_of(w), O.detect_of(w), 0.0, 1.0, pix)
+    band = (ref["margin_t"] < 1e-3) | (ref["margin_c"] < 1e-5)
+    ev = outs[0]["events"].cpu().numpy().reshape(-1)
+    n = outs[0]["spp"].cpu().numpy().reshape(-1)
+    agree = ((ev == ref["events"]) & (n == ref["n"])) | band
+    assert agree.mean() > 0.9
+    r.close()
+    runner.close()
+
+
+def test_batch_rejects_mismatched_schedule():
+    from paper_2408_07996_gb300 import McevError
+    ws = _jobs()[:2]
+    rs = _renderers(ws)
+    rs[1].set_params(spp_min=32)
+    with pytest.raises(McevError, match="ARG"):
+        render_events_batch(rs[0], [(rs[0], 0.0, 1.0), (rs[1], 0.0, 1.0)], *SCHED)
+    with pytest.raises(McevError, match="ARG"):
+        render_events_batch(rs[0], [(rs[0], 0.0, 1.0), (rs[0], 0.0, 1.0)], *SCHED)
+    for r in rs:
+        r.close()
+
+
+def test_autotuner_keeps_results():
+    from paper_2408_07996_gb300.autotune import tune_batch
+    ws = _jobs()[:3]
+    rs = _renderers(ws)
+    runner = Renderer(8, 8)
+    render_events_batch(runner, [(r, 0.0, 1.0) for r in rs], *SCHED)        # references
+    states = [r.get_state().clone() for r in rs]
+    base, _ = render_events_batch(runner, [(r, 1.0, 2.0) for r in rs], *SCHED)
+    for r, s in zip(rs, states):
+        r.set_state(s)
+    res = tune_batch(runner, rs, (1.0, 2.0), SCHEDULE, wavefronts=(1 << 20, 1 << 22), windows=(2, 8),
+                     leaf_sizes=(2, 4))
+    assert len(res["trials"]) == 8
+    tuned, _ = render_events_batch(runner, [(r, 1.0, 2.0) for r in rs], *SCHED)
+    for a, b in zip(base, tuned):
+        for k in ("events", "spp", "mean"):
+            assert torch.equal(a[k], b[k])
+    for r in rs:
+        r.close()
+    runner.close()
