@@ -47,6 +47,8 @@ def lib():
                                        vp, vp, vp, d, i32, vp, vp, vp, vp, i32, i32, vp]
         L.orc_scene_create.restype = vp
         L.orc_scene_free.argtypes = [vp]
+        L.orc_scene_set_texture.argtypes = [vp, vp, vp, vp, i32, i32, vp]
+        L.orc_scene_set_emission.argtypes = [vp, vp]
         L.orc_closest_hit.argtypes = [vp, d, vp, vp, d, d, C.c_int, P(d), P(i32), P(i32)]
         L.orc_closest_hit.restype = C.c_int
         L.orc_trace_samples.argtypes = [vp, vp, d, vp, i64, i64, i64, vp, vp]
@@ -169,6 +171,9 @@ class OracleScene:
             _p(sc.cam_target), _p(sc.cam_up), float(sc.fov_deg), sc.mat_type.shape[0],
             _p(sc.mat_type), _p(sc.mat_albedo), _p(sc.mat_rough), _p(sc.mat_emit),
             0 if env is None else env.shape[1], 0 if env is None else env.shape[0], _p(env))
+        self._sc = sc
+        if getattr(sc, "texture", None) is not None and sc.uvs is not None and sc.mat_textured is not None:
+            self.set_texture(sc.texture)
         self._keep = None
 
     def __del__(self):
@@ -183,6 +188,22 @@ class OracleScene:
         hit = lib().orc_closest_hit(self.ptr, time, _p(o), _p(d), t_min, t_max, int(use_bvh),
                                     C.byref(t), C.byref(i), C.byref(p))
         return bool(hit), t.value, i.value, p.value
+
+    def set_texture(self, texture):
+        """Replaces the RGB albedo texture [H, W, 3] (the scene must carry
+        texture coordinates and textured-material flags)."""
+        sc = self._sc
+        tex = np.ascontiguousarray(texture, np.float32)
+        uvs = np.ascontiguousarray(sc.uvs, np.float32)
+        tris = np.ascontiguousarray(sc.triangles, np.int32)
+        mtex = np.ascontiguousarray(sc.mat_textured, np.int32)
+        lib().orc_scene_set_texture(self.ptr, _p(uvs), _p(tris), _p(mtex), tex.shape[1], tex.shape[0], _p(tex))
+
+    def set_emission(self, emission):
+        """Replaces the emitted radiance of the scene's emissive materials."""
+        e = np.ascontiguousarray(emission, np.float32)
+        assert e.shape == (len(self._sc.mat_emit),)
+        lib().orc_scene_set_emission(self.ptr, _p(e))
 
     def camera_ray(self, p: "Params", time, fx, fy):
         o, d = np.zeros(3), np.zeros(3)

@@ -53,6 +53,16 @@ orc_scene* orc_scene_create(
     int32_t env_w, int32_t env_h, const float* env);
 void orc_scene_free(orc_scene* s);
 
+/* Texturing: per-vertex texture coordinates [n_vertices][2], per-material
+ * flag (1 = Lambertian albedo from the texture) and an RGB texture
+ * [tex_h][tex_w][3]; a textured hit takes the Rec. 709 luminance of the
+ * nearest texel at its barycentrically interpolated, wrapped coordinates. */
+void orc_scene_set_texture(orc_scene* s, const float* uvs, const int32_t* triangles, const int32_t* mat_textured,
+                           int32_t tex_w, int32_t tex_h, const float* texture);
+/* Emitted radiance per material replacing the scene's table for the
+ * materials the table makes emissive (the emitter set stays fixed). */
+void orc_scene_set_emission(orc_scene* s, const float* emission);
+
 /* render settings shared by every oracle entry point */
 typedef struct {
     int32_t width, height;

@@ -77,12 +77,18 @@ struct orc_scene {
     int32_t nmat;
     int32_t* mtype;
     double *malb, *mrough, *memit;
+    double* memit0;        /* the table's emission: fixes which materials emit */
     /* environment */
     int32_t ew, eh;
     double* env;           /* [eh][ew] */
     double* marg;          /* [eh+1] row CDF, values rounded to FP32 */
     double* cond;          /* [eh][ew+1] column CDFs, values rounded to FP32 */
     double env_total;      /* sum_ij L_ij sin(theta_i) */
+    /* texturing */
+    double* tri_uv;        /* [nt][6] or NULL */
+    int32_t* mat_tex;      /* [nmat] or NULL */
+    int32_t tw, th;
+    double* tex;           /* [th][tw][3] */
     /* emissive (instance, triangle) pairs in instance-then-triangle order */
     int64_t n_lights;
     int32_t* light_inst;
@@ -282,7 +288,9 @@ orc_scene* orc_scene_create(
     s->malb = (double*)malloc(sizeof(double) * n_materials);
     s->mrough = (double*)malloc(sizeof(double) * n_materials);
     s->memit = (double*)malloc(sizeof(double) * n_materials);
+    s->memit0 = (double*)malloc(sizeof(double) * n_materials);
     for (int i = 0; i < n_materials; ++i) {
+        s->memit0[i] = mat_emit[i];
         s->mtype[i] = mat_type[i];
         s->malb[i] = mat_albedo[i];
         s->mrough[i] = mat_rough[i];
@@ -327,10 +335,32 @@ void orc_scene_free(orc_scene* s) {
     }
     free(s->meshes); free(s->tv); free(s->tri_mat); free(s->inst_mesh); free(s->inst_mat);
     free(s->key_t); free(s->key_xf); free(s->cam_eye); free(s->cam_tgt); free(s->cam_up);
-    free(s->mtype); free(s->malb); free(s->mrough); free(s->memit);
+    free(s->mtype); free(s->malb); free(s->mrough); free(s->memit); free(s->memit0);
     free(s->env); free(s->marg); free(s->cond);
     free(s->light_inst); free(s->light_prim);
+    free(s->tri_uv); free(s->mat_tex); free(s->tex);
     free(s);
+}
+
+void orc_scene_set_texture(orc_scene* s, const float* uvs, const int32_t* triangles, const int32_t* mat_textured,
+                           int32_t tex_w, int32_t tex_h, const float* texture) {
+    free(s->tri_uv); free(s->mat_tex); free(s->tex);
+    s->tri_uv = (double*)malloc(sizeof(double) * 6 * (s->nt > 0 ? s->nt : 1));
+    for (int64_t t = 0; t < s->nt; ++t)
+        for (int c = 0; c < 3; ++c)
+            for (int a = 0; a < 2; ++a)
+                s->tri_uv[6 * t + 2 * c + a] = uvs[2 * (int64_t)triangles[3 * t + c] + a];
+    s->mat_tex = (int32_t*)malloc(sizeof(int32_t) * s->nmat);
+    for (int m = 0; m < s->nmat; ++m) s->mat_tex[m] = mat_textured[m];
+    s->tw = tex_w;
+    s->th = tex_h;
+    s->tex = (double*)malloc(sizeof(double) * 3 * (int64_t)tex_w * tex_h);
+    for (int64_t i = 0; i < 3 * (int64_t)tex_w * tex_h; ++i) s->tex[i] = texture[i];
+}
+
+void orc_scene_set_emission(orc_scene* s, const float* emission) {
+    for (int m = 0; m < s->nmat; ++m)
+        if (s->memit0[m] > 0.0) s->memit[m] = emission[m];
 }
 
 /* ------------------------------------------------------------------ */
@@ -901,6 +931,31 @@ static double trace_path(const orc_scene* s, const orc_params* p, const oframe* 
         v3 ng = hit_normal(s, fr, &h);
         v3 wo = scl(d, -1.0);
         int mat = material_of(s, h.inst, h.prim);
+        double alb = s->malb[mat];
+        if (s->tex && s->mat_tex && s->mat_tex[mat]) {
+            /* barycentric coordinates of the hit in the object-space triangle */
+            const double* v = s->tv + 9 * h.prim;
+            v3 a = mk(v[0], v[1], v[2]), b = mk(v[3], v[4], v[5]), c = mk(v[6], v[7], v[8]);
+            v3 po = xf_point(fr->inst[h.inst].Minv, P);
+            v3 e1 = sub(b, a), e2 = sub(c, a), vp = sub(po, a);
+            double d00 = dot(e1, e1), d01 = dot(e1, e2), d11 = dot(e2, e2), d20 = dot(vp, e1), d21 = dot(vp, e2);
+            double den = d00 * d11 - d01 * d01;
+            double b1 = (d11 * d20 - d01 * d21) / den, b2 = (d00 * d21 - d01 * d20) / den, b0 = 1.0 - b1 - b2;
+            const double* uv = s->tri_uv + 6 * h.prim;
+            double u = b0 * uv[0] + b1 * uv[2] + b2 * uv[4];
+            double vv = b0 * uv[1] + b1 * uv[3] + b2 * uv[5];
+            if (!isfinite(u)) u = 0.0; /* degenerate triangle */
+            if (!isfinite(vv)) vv = 0.0;
+            u -= floor(u);
+            vv -= floor(vv);
+            int ix = (int)(u * s->tw), iy = (int)(vv * s->th);
+            if (ix > s->tw - 1) ix = s->tw - 1;
+            if (iy > s->th - 1) iy = s->th - 1;
+            int64_t texel = (int64_t)iy * s->tw + ix;
+            const double* rgb = s->tex + 3 * texel;
+            alb = 0.2126 * rgb[0] + 0.7152 * rgb[1] + 0.0722 * rgb[2];
+            sig = fnv(sig, (uint32_t)texel);
+        }
         uint32_t flags = 0;
         double cos_o = dot(ng, wo);
         if (s->memit[mat] > 0.0 && cos_o > 0.0) {
@@ -916,7 +971,7 @@ static double trace_path(const orc_scene* s, const orc_params* p, const oframe* 
             }
             L += beta * w * s->memit[mat];
         }
-        if (depth == p->max_depth || !(s->malb[mat] > 0.0)) {
+        if (depth == p->max_depth || !(alb > 0.0)) {
             sig = fnv(sig, flags);
             break;
         }
@@ -925,7 +980,7 @@ static double trace_path(const orc_scene* s, const orc_params* p, const oframe* 
         onb(n, &tb, &bt);
         double wol[3] = {dot(wo, tb), dot(wo, bt), dot(wo, n)};
         int type = s->mtype[mat];
-        double alb = s->malb[mat], rough = s->mrough[mat];
+        double rough = s->mrough[mat];
         /* next-event estimation */
         if (p->nee && (env_ok || have_area)) {
             rng4(fr, (uint32_t)pix, (uint32_t)k, (uint32_t)(depth + 1), 0u, x);

@@ -10,6 +10,8 @@ from .procedural import (  # noqa: F401
     Scene,
     Workload,
     WORKLOADS,
+    albedo_texture,
+    textured_room,
     BATCH_RESOLUTIONS,
     batch_workloads,
     cornell_box,
@@ -17,6 +19,7 @@ from .procedural import (  # noqa: F401
     furnace_sphere,
     icosphere_field,
     plane_under_env,
+    textured_plane,
     sky_texture,
     static_variant,
     terrain_with_boxes,

@@ -46,6 +46,9 @@ class Scene:
     mat_rough: np.ndarray         # float32 [Nm]
     mat_emit: np.ndarray          # float32 [Nm]
     env: np.ndarray | None = None  # float32 [H, W]
+    uvs: np.ndarray | None = None          # float32 [Nv, 2] texture coordinates, optional
+    mat_textured: np.ndarray | None = None  # int32 [Nm]: 1 = Lambertian albedo from the texture
+    texture: np.ndarray | None = None      # float32 [Ht, Wt, 3] RGB albedo texture, optional
 
     def __post_init__(self):
         self.vertices = np.ascontiguousarray(self.vertices, np.float32).reshape(-1, 3)
@@ -65,6 +68,13 @@ class Scene:
         if self.env is not None:
             self.env = np.ascontiguousarray(self.env, np.float32)
             assert self.env.ndim == 2
+        if self.uvs is not None:
+            self.uvs = np.ascontiguousarray(self.uvs, np.float32).reshape(-1, 2)
+        if self.mat_textured is not None:
+            self.mat_textured = np.ascontiguousarray(self.mat_textured, np.int32).reshape(-1)
+        if self.texture is not None:
+            self.texture = np.ascontiguousarray(self.texture, np.float32)
+            assert self.texture.ndim == 3 and self.texture.shape[2] == 3
 
     @property
     def n_triangles(self) -> int:
@@ -456,6 +466,18 @@ def plane_under_env(albedo: float = 0.5, env_value: float = 2.0, half: float = 5
                  [DIFFUSE], [albedo], [0.0], [0.0], env)
 
 
+def textured_plane(texture: np.ndarray, repeat: float = 3.0, env_value: float = 2.0, half: float = 0.5,
+                   height: float = 1.0) -> Scene:
+    """plane_under_env with texture coordinates (u, v) = repeat * ((x, z) +
+    half) / (2 half) and a textured Lambertian material: with BSDF sampling
+    only, each path's radiance is env_value times the Rec. 709 luminance of
+    the nearest texel at the wrapped coordinates of its first hit."""
+    sc = plane_under_env(0.5, env_value, half, height)
+    uv = repeat * (sc.vertices[:, [0, 2]].astype(np.float64) + half) / (2.0 * half)
+    return replace(sc, uvs=uv.astype(np.float32), mat_textured=np.array([1], np.int32),
+                   texture=np.ascontiguousarray(texture, np.float32))
+
+
 def empty_env(env_value: float = 3.0) -> Scene:
     """No geometry at all, constant environment: every path's radiance is
     env_value (the degenerate zero-triangle scene)."""
@@ -509,6 +531,10 @@ def workload(name: str, **over) -> Workload:
         sc = icosphere_field(20240816)
         w = Workload(name, sc, 512, 512, list(sc.key_times), spp_min=256, spp_batch=32,
                      spp_max=4096, C=0.25, alpha=0.01, max_depth=4, seed=20240816)
+    elif name == "diff256":
+        sc = textured_room(20240819)
+        w = Workload(name, sc, 256, 256, [0.0, 1.0], spp_min=64, spp_batch=64, spp_max=64,
+                     C=0.2, alpha=0.05, max_depth=3, seed=20240819)
     elif name == "terrain720p":
         sc = terrain_with_boxes(20240817)
         w = Workload(name, sc, 1280, 720, list(sc.key_times), spp_min=512, spp_batch=64,
@@ -519,6 +545,71 @@ def workload(name: str, **over) -> Workload:
     for k, v in over.items():
         setattr(w, k, v)
     return w
+
+
+def albedo_texture(size: int = 512, seed: int = 0, lo: float = 0.2, hi: float = 0.8) -> np.ndarray:
+    """RGB albedo texture [size, size, 3]: smooth random blobs in [lo, hi]."""
+    rng = np.random.default_rng(seed)
+    k = np.fft.fftfreq(size)[:, None] ** 2 + np.fft.fftfreq(size)[None, :] ** 2
+    out = np.empty((size, size, 3))
+    for c in range(3):
+        spec = (rng.normal(size=(size, size)) + 1j * rng.normal(size=(size, size))) * np.exp(-k * 400.0)
+        f = np.real(np.fft.ifft2(spec))
+        f = (f - f.min()) / (f.max() - f.min() + 1e-12)
+        out[..., c] = lo + (hi - lo) * f
+    return out.astype(np.float32)
+
+
+def textured_room(seed: int = 20240819, grid: int = 158, tex_size: int = 512, shift: float = 0.05,
+                  texture: np.ndarray | None = None) -> Scene:
+    """Differentiation scene (config 5): a (grid-1)^2*2-triangle floor (about
+    50k triangles at grid 158) carrying an RGB albedo texture, a few
+    untextured boxes, and 4 one-sided emissive quads (one material each)
+    above it.  Camera looks down at the floor and shifts by `shift` along x
+    between t = 0 and t = 1."""
+    rng = np.random.default_rng(seed)
+    mb = _MeshBuilder()
+    xs = np.linspace(-2.0, 2.0, grid)
+    X, Z = np.meshgrid(xs, xs, indexing="ij")
+    verts = np.stack([X, np.zeros_like(X), Z], -1).reshape(-1, 3)
+    i, j = np.meshgrid(np.arange(grid - 1), np.arange(grid - 1), indexing="ij")
+    v00 = (i * grid + j).reshape(-1)
+    tris = np.concatenate([np.stack([v00, v00 + 1, v00 + grid + 1], -1),
+                           np.stack([v00, v00 + grid + 1, v00 + grid], -1)])
+    uv_floor = np.stack([(X + 2.0) / 4.0, (Z + 2.0) / 4.0], -1).reshape(-1, 2)
+    mb.add(verts, tris, 0)
+    uvs = [uv_floor]
+    n_box = 3
+    for b in range(n_box):
+        c = rng.uniform(-1.2, 1.2, size=2)
+        h = float(rng.uniform(0.2, 0.6))
+        for q in _box_faces((c[0] - 0.25, 0.0, c[1] - 0.25), (c[0] + 0.25, h, c[1] + 0.25), rot_y=float(rng.uniform(0, 3))):
+            v, t = _quad(*q)
+            mb.add(v, t, 1 + b)
+            uvs.append(np.zeros((4, 2)))
+    n_lights = 4
+    for l in range(n_lights):
+        cx, cz = [(-1.0, -1.0), (1.0, -1.0), (-1.0, 1.0), (1.0, 1.0)][l]
+        y = 2.0
+        v, t = _quad((cx - 0.3, y, cz - 0.3), (cx + 0.3, y, cz - 0.3), (cx + 0.3, y, cz + 0.3), (cx - 0.3, y, cz + 0.3))
+        mb.add(v, t, 1 + n_box + l)
+        uvs.append(np.zeros((4, 2)))
+    verts, tris, tmat = mb.arrays()
+    nm = 1 + n_box + n_lights
+    mat_type = np.zeros(nm, np.int32)
+    mat_albedo = np.array([0.5] + [float(rng.uniform(0.3, 0.8)) for _ in range(n_box)] + [0.0] * n_lights)
+    mat_emit = np.array([0.0] * (1 + n_box) + [float(rng.uniform(4.0, 8.0)) for _ in range(n_lights)])
+    textured = np.zeros(nm, np.int32)
+    textured[0] = 1
+    times = np.array([0.0, 1.0])
+    xf, _, _, up = _static_keys(times, 1, IDENTITY, (0, 0, 0), (0, 0, 0), (0, 0, -1))
+    eye = np.array([[0.0, 3.2, 0.0], [shift, 3.2, 0.0]])
+    target = np.array([[0.0, 0.0, 0.0], [shift, 0.0, 0.0]])
+    up = np.array([[0.0, 0.0, -1.0], [0.0, 0.0, -1.0]])
+    tex = albedo_texture(tex_size, seed) if texture is None else texture
+    return Scene(verts, tris, tmat, [[0, tris.shape[0]]], [0], [-1], times, xf, eye, target, up, 70.0,
+                 mat_type, mat_albedo, np.zeros(nm), mat_emit, None,
+                 uvs=np.concatenate(uvs).astype(np.float32), mat_textured=textured, texture=tex)
 
 
 WORKLOADS = ("cornell64", "spheres512", "terrain720p")
