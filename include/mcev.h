@@ -90,6 +90,9 @@ typedef struct {
     const float* mat_emit;        /* [n_materials] */
     int32_t env_w, env_h;
     const float* env;             /* [env_h][env_w] or NULL */
+    const float* uvs;             /* [n_vertices][2] texture coordinates, or NULL */
+    const int32_t* mat_textured;  /* [n_materials]: 1 = Lambertian albedo read from the texture set by
+                                     mcev_set_texture (luminance of the nearest texel), or NULL */
 } mcev_scene_desc;
 
 /* Render settings (mcev_set_params). */
@@ -197,6 +200,40 @@ mcev_status mcev_render_reference(mcev_ctx* ctx, double t0, int32_t spp);
 mcev_status mcev_render_events(mcev_ctx* ctx, double t0, double t1, float C, float alpha,
                                int32_t spp_batch, int32_t spp_max, int8_t* events_out,
                                int32_t* spp_out, float* mean_out, mcev_stats* stats_out);
+
+/* ------------------------------------------------------------------------
+ * Differentiable rendering (path-replay adjoint).  The texture and the
+ * emission values are caller-owned DEVICE buffers that the library reads at
+ * render time (keep them alive and unchanged while a call runs); setting
+ * them does not copy.  Gradients cover textured Lambertian albedo and
+ * emitted radiance; geometry and visibility are held fixed.
+ * ------------------------------------------------------------------------ */
+
+/* RGB albedo texture [height][width][3] (device float) used by textured
+ * materials; NULL restores the materials' table albedo.  Errors: ARG. */
+mcev_status mcev_set_texture(mcev_ctx* ctx, const float* texture, int32_t width, int32_t height);
+
+/* Emitted radiance per material (device float [n_materials]) overriding the
+ * scene's table for the materials that the table makes emissive (value > 0);
+ * entries of the other materials are ignored, since the set of emitters that
+ * next-event estimation samples is fixed by the scene.  An override <= 0
+ * turns that emitter dark.  NULL restores the table.
+ * Errors: ARG (n != material count). */
+mcev_status mcev_set_emission(mcev_ctx* ctx, const float* emission, int32_t n_materials);
+
+/* Per-pixel mean of ln(L + eps) over samples 0..spp-1 at time t (every
+ * pixel the same count; the reference state is not touched).
+ *   mean_out: device float [H*W].  Errors: ARG, STATE, OOM, CUDA. */
+mcev_status mcev_render_mean(mcev_ctx* ctx, double t, int32_t spp, float* mean_out);
+
+/* Adjoint of mcev_render_mean (path-replay backpropagation): given
+ * grad_mean = d loss / d mean (device float [H*W]), ADDS d loss / d texel
+ * RGB to grad_texture (device float [th][tw][3], may be NULL) and
+ * d loss / d emitted radiance to grad_emission (device float [n_materials],
+ * may be NULL), replaying the same samples with the same random numbers.
+ * Errors: ARG, STATE, OOM, CUDA. */
+mcev_status mcev_backward(mcev_ctx* ctx, double t, int32_t spp, const float* grad_mean, float* grad_texture,
+                          float* grad_emission);
 
 /* One frame pair of a batched render. */
 typedef struct {

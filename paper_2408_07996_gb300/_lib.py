@@ -34,6 +34,7 @@ class SceneDesc(C.Structure):
         ("n_materials", C.c_int32), ("mat_type", C.c_void_p), ("mat_albedo", C.c_void_p),
         ("mat_rough", C.c_void_p), ("mat_emit", C.c_void_p),
         ("env_w", C.c_int32), ("env_h", C.c_int32), ("env", C.c_void_p),
+        ("uvs", C.c_void_p), ("mat_textured", C.c_void_p),
     ]
 
 
@@ -97,6 +98,10 @@ SIGNATURES = {
     "mcev_render_reference": (C.c_int, [C.c_void_p, C.c_double, C.c_int32]),
     "mcev_render_events": (C.c_int, [C.c_void_p, C.c_double, C.c_double, C.c_float, C.c_float, C.c_int32,
                                      C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(Stats)]),
+    "mcev_set_texture": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32]),
+    "mcev_set_emission": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
+    "mcev_render_mean": (C.c_int, [C.c_void_p, C.c_double, C.c_int32, C.c_void_p]),
+    "mcev_backward": (C.c_int, [C.c_void_p, C.c_double, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
     "mcev_render_events_batch": (C.c_int, [C.c_void_p, C.POINTER(JobDesc), C.c_int32, C.c_float, C.c_float,
                                            C.c_int32, C.c_int32, C.POINTER(Stats)]),
     "mcev_trace_samples": (C.c_int, [C.c_void_p, C.c_double, C.c_void_p, C.c_int64, C.c_int64, C.c_int32,

@@ -119,6 +119,10 @@ class Renderer:
             mat_emit=np.ascontiguousarray(scene.mat_emit, np.float32),
         )
         env = None if scene.env is None else np.ascontiguousarray(scene.env, np.float32)
+        uvs = getattr(scene, "uvs", None)
+        uvs = None if uvs is None else np.ascontiguousarray(uvs, np.float32)
+        mtex = getattr(scene, "mat_textured", None)
+        mtex = None if mtex is None else np.ascontiguousarray(mtex, np.int32)
         d = L.SceneDesc(
             n_vertices=arrs["vertices"].shape[0], vertices=_ptr(arrs["vertices"]),
             n_triangles=arrs["triangles"].shape[0], triangles=_ptr(arrs["triangles"]),
@@ -132,8 +136,12 @@ class Renderer:
             n_materials=arrs["mat_type"].shape[0], mat_type=_ptr(arrs["mat_type"]),
             mat_albedo=_ptr(arrs["mat_albedo"]), mat_rough=_ptr(arrs["mat_rough"]),
             mat_emit=_ptr(arrs["mat_emit"]),
-            env_w=0 if env is None else env.shape[1], env_h=0 if env is None else env.shape[0], env=_ptr(env))
+            env_w=0 if env is None else env.shape[1], env_h=0 if env is None else env.shape[0], env=_ptr(env),
+            uvs=_ptr(uvs), mat_textured=_ptr(mtex))
         L.check(self.lib.mcev_scene_upload(self.ctx, C.byref(d)), self.ctx, "mcev_scene_upload")
+        tex = getattr(scene, "texture", None)
+        if tex is not None:
+            self.set_texture(torch.from_numpy(np.ascontiguousarray(tex, np.float32)).to(self.device))
 
     def build_bvh(self, sah_bins: int = 32, max_leaf: int = 4) -> None:
         L.check(self.lib.mcev_build_bvh(self.ctx, sah_bins, max_leaf), self.ctx, "mcev_build_bvh")
@@ -186,6 +194,35 @@ class Renderer:
                                             _tptr(sig)), self.ctx, "mcev_trace_samples")
         return Lo, sig
 
+    # ------------------------------------------------------------ differentiable rendering
+    def set_texture(self, texture: torch.Tensor | None) -> None:
+        """RGB albedo texture [H, W, 3] on the device (kept by reference)."""
+        if texture is None:
+            L.check(self.lib.mcev_set_texture(self.ctx, None, 0, 0), self.ctx, "mcev_set_texture")
+            self._texture = None
+            return
+        assert texture.is_cuda and texture.dtype == torch.float32 and texture.is_contiguous()
+        self._texture = texture
+        L.check(self.lib.mcev_set_texture(self.ctx, _tptr(texture), texture.shape[1], texture.shape[0]), self.ctx,
+                "mcev_set_texture")
+
+    def set_emission(self, emission: torch.Tensor | None) -> None:
+        """Emitted radiance per material on the device (kept by reference)."""
+        self._emission = emission
+        n = 0 if emission is None else emission.numel()
+        L.check(self.lib.mcev_set_emission(self.ctx, _tptr(emission), n), self.ctx, "mcev_set_emission")
+
+    def render_mean(self, t: float, spp: int) -> torch.Tensor:
+        out = torch.empty((self.height, self.width), dtype=torch.float32, device=self.device)
+        L.check(self.lib.mcev_render_mean(self.ctx, float(t), int(spp), _tptr(out)), self.ctx, "mcev_render_mean")
+        return out
+
+    def backward(self, t: float, spp: int, grad_mean: torch.Tensor, grad_texture: torch.Tensor | None,
+                 grad_emission: torch.Tensor | None) -> None:
+        g = grad_mean.to(device=self.device, dtype=torch.float32).contiguous()
+        L.check(self.lib.mcev_backward(self.ctx, float(t), int(spp), _tptr(g), _tptr(grad_texture),
+                                       _tptr(grad_emission)), self.ctx, "mcev_backward")
+
     def state_bytes(self) -> int:
         return int(self.lib.mcev_state_bytes(self.ctx))
 
@@ -228,3 +265,49 @@ def render_events_batch(runner: Renderer, jobs, C_: float, alpha: float, spp_bat
                                                 int(spp_batch), int(spp_max), C.byref(st) if stats else None),
             runner.ctx, "mcev_render_events_batch")
     return outs, (st.as_dict() if stats else None)
+
+
+class EventFrames(torch.autograd.Function):
+    """(texture, emission) -> per-pixel mean ln(L + eps) at t0 and t1.
+
+    The backward pass is the library's path-replay adjoint (mcev_backward):
+    gradients with respect to the RGB albedo texture of textured Lambertian
+    materials and to every material's emitted radiance."""
+
+    @staticmethod
+    def forward(ctx, texture, emission, renderer, t0, t1, spp):
+        renderer.set_texture(texture)
+        renderer.set_emission(emission)
+        m0 = renderer.render_mean(t0, spp)
+        m1 = renderer.render_mean(t1, spp)
+        ctx.save_for_backward(texture, emission)
+        ctx.renderer, ctx.frame = renderer, (t0, t1, spp)
+        return m0, m1
+
+    @staticmethod
+    def backward(ctx, g0, g1):
+        texture, emission = ctx.saved_tensors
+        r = ctx.renderer
+        t0, t1, spp = ctx.frame
+        gt = torch.zeros_like(texture)
+        ge = torch.zeros_like(emission)
+        r.set_texture(texture)
+        r.set_emission(emission)
+        if g0 is not None:
+            r.backward(t0, spp, g0, gt, ge)
+        if g1 is not None:
+            r.backward(t1, spp, g1, gt, ge)
+        return gt, ge, None, None, None, None
+
+
+def event_loss(m0: torch.Tensor, m1: torch.Tensor, target_events: torch.Tensor, C_: float,
+               tau: float = 0.05) -> torch.Tensor:
+    """Smooth event loss: where the target has an event of polarity p, a
+    softplus push of p * (m1 - m0) above C; elsewhere a softplus push of
+    |m1 - m0| below C (temperature tau)."""
+    d = m1 - m0
+    p = target_events.to(d.dtype)
+    on = target_events != 0
+    on_term = torch.nn.functional.softplus((C_ - p * d) / tau)
+    off_term = torch.nn.functional.softplus((d.abs() - C_) / tau)
+    return torch.where(on, on_term, off_term).sum()

@@ -82,6 +82,7 @@ struct mcev_ctx {
     bool env_ok = false;
     int sah_bins = 32, max_leaf = 4;
     int bvh_depth = 0;
+    std::vector<float> tri_uv;              // [tri][6] texture coordinates (empty: no uvs)
     std::vector<char> inst_static;          // keyframes never change
     std::vector<float> static_vtx;          // world-space triangles of static instances
     bool has_static = false;
@@ -89,7 +90,7 @@ struct mcev_ctx {
     float static_lo[3], static_hi[3];
 
     // device scene
-    DevBuf d_nodes, d_tris, d_mats, d_env, d_marg, d_cond, d_tpdf;
+    DevBuf d_nodes, d_tris, d_uv, d_mats, d_env, d_marg, d_cond, d_tpdf;
     DevScene dsc{};
     Frame frames[2];
 
@@ -215,6 +216,11 @@ mcev_status ev_mark(mcev_ctx* ctx, int cls, bool start) {
     return MCEV_OK;
 }
 
+const float* tri_uv_of(const mcev_ctx* ctx, int64_t prim) {
+    static const float zeros[6] = {0, 0, 0, 0, 0, 0};
+    return ctx->tri_uv.empty() ? zeros : &ctx->tri_uv[6 * (size_t)prim];
+}
+
 // ---------------------------------------------------------------- affine helpers (FP64)
 void affine_inverse(const double* M, double* R) {
     const double a = M[0], b = M[1], c = M[2], d = M[4], e = M[5], f = M[6], g = M[8], h = M[9], i = M[10];
@@ -259,8 +265,12 @@ struct TriSrc {
     int32_t prim, mat, inst;
 };
 
+// texture coordinates of the uploaded triangle `prim` (6 floats; zeros without uvs)
+const float* tri_uv_of(const mcev_ctx* ctx, int64_t prim);
+
 mcev_status build_one(mcev_ctx* ctx, const std::vector<TriSrc>& src, std::vector<Node>& nodes,
-                      std::vector<float4>& tris, int& root, float lo_out[3], float hi_out[3], int& depth) {
+                      std::vector<float4>& tris, std::vector<float2>& uvs, int& root, float lo_out[3],
+                      float hi_out[3], int& depth) {
     const int n = (int)src.size();
     std::vector<float> lo(3 * (size_t)n), hi(3 * (size_t)n), ce(3 * (size_t)n);
     for (int i = 0; i < n; ++i) {
@@ -300,6 +310,8 @@ mcev_status build_one(mcev_ctx* ctx, const std::vector<TriSrc>& src, std::vector
         tris.push_back(t0);
         tris.push_back(t1);
         tris.push_back(t2);
+        const float* tu = tri_uv_of(ctx, s.prim);
+        for (int c = 0; c < 3; ++c) uvs.push_back(make_float2(tu[2 * c], tu[2 * c + 1]));
         for (int a = 0; a < 3; ++a) {
             lo_out[a] = std::min(lo_out[a], std::min(v[a], std::min(v[3 + a], v[6 + a])));
             hi_out[a] = std::max(hi_out[a], std::max(v[a], std::max(v[3 + a], v[6 + a])));
@@ -311,6 +323,7 @@ mcev_status build_one(mcev_ctx* ctx, const std::vector<TriSrc>& src, std::vector
 mcev_status build_blas(mcev_ctx* ctx) {
     std::vector<Node> nodes;
     std::vector<float4> tris;
+    std::vector<float2> uvs;
     tris.reserve(ctx->vtx.size() / 3);
     int depth = 0;
     const int ni = ctx->n_inst, nk = ctx->n_keys;
@@ -332,7 +345,7 @@ mcev_status build_blas(mcev_ctx* ctx) {
             const int64_t prim = m.first_tri + t;
             src[t] = TriSrc{&ctx->vtx[9 * (size_t)prim], (int32_t)prim, ctx->tri_mat[prim], -1};
         }
-        ST(build_one(ctx, src, nodes, tris, m.root, m.lo, m.hi, depth));
+        ST(build_one(ctx, src, nodes, tris, uvs, m.root, m.lo, m.hi, depth));
     }
     // merged static geometry in world space (keyframe 0 transform, FP64 -> FP32)
     ctx->static_vtx.clear();
@@ -366,13 +379,17 @@ mcev_status build_blas(mcev_ctx* ctx) {
     }
     ctx->static_root = -1;
     ctx->has_static = n_static_tris > 0;
-    if (ctx->has_static) ST(build_one(ctx, ssrc, nodes, tris, ctx->static_root, ctx->static_lo, ctx->static_hi, depth));
+    if (ctx->has_static)
+        ST(build_one(ctx, ssrc, nodes, tris, uvs, ctx->static_root, ctx->static_lo, ctx->static_hi, depth));
     if (nodes.empty()) {
         Node none;
         std::memset(&none, 0, sizeof none);
         nodes.push_back(none);
     }
-    if (tris.empty()) tris.push_back(make_float4(0, 0, 0, 0));
+    if (tris.empty()) {
+        tris.push_back(make_float4(0, 0, 0, 0));
+        uvs.push_back(make_float2(0, 0));
+    }
     // a traversal pushes at most one entry per inner-node level
     if (depth > MCEV_STACK_HOST)
         return fail(ctx, MCEV_ERR_ARG, "BVH depth %d exceeds the traversal stack (%d)", depth, MCEV_STACK_HOST);
@@ -381,6 +398,12 @@ mcev_status build_blas(mcev_ctx* ctx) {
     ST(upload(ctx, ctx->d_tris, tris.data(), tris.size() * sizeof(float4)));
     ctx->dsc.nodes = (const Node*)ctx->d_nodes.ptr;
     ctx->dsc.tris = (const float4*)ctx->d_tris.ptr;
+    if (!ctx->tri_uv.empty()) {
+        ST(upload(ctx, ctx->d_uv, uvs.data(), uvs.size() * sizeof(float2)));
+        ctx->dsc.tri_uv = (const float2*)ctx->d_uv.ptr;
+    } else {
+        ctx->dsc.tri_uv = nullptr;
+    }
     for (auto& f : ctx->frames) f.valid = false;
     return MCEV_OK;
 }
@@ -537,7 +560,9 @@ mcev_status frame_setup(mcev_ctx* ctx, double t, int slot) {
         const int mat = ctx->inst_mat[i] >= 0 ? ctx->inst_mat[i] : ctx->tri_mat[prim];
         lights[4 * l + 0] = make_float4((float)p[0][0], (float)p[0][1], (float)p[0][2], ctx->mat_emit[mat]);
         lights[4 * l + 1] = make_float4((float)p[1][0], (float)p[1][1], (float)p[1][2], (float)(0.5 * len));
-        lights[4 * l + 2] = make_float4((float)p[2][0], (float)p[2][1], (float)p[2][2], 0.0f);
+        float mat_bits;
+        std::memcpy(&mat_bits, &mat, 4);
+        lights[4 * l + 2] = make_float4((float)p[2][0], (float)p[2][1], (float)p[2][2], mat_bits);
         lights[4 * l + 3] = make_float4((float)(cr[0] / len), (float)(cr[1] / len), (float)(cr[2] / len), 0.0f);
     }
     const size_t nb_t = tlas.size() * sizeof(Node), nb_i = inst.size() * sizeof(float4),
@@ -607,7 +632,7 @@ mcev_status frame_setup(mcev_ctx* ctx, double t, int slot) {
 mcev_status ensure_wave(mcev_ctx* ctx) {
     const int64_t cap = ctx->params.wavefront > 0 ? ctx->params.wavefront : ((int64_t)1 << 25);
     if (ctx->d_wave.ptr && ctx->wave.cap == cap) return MCEV_OK;
-    const size_t per = 4 * 3 + 4 * 2 + 8 + 16 * 2 * 2 + 16 + 16 * 2 + 4;
+    const size_t per = 4 * 3 + 4 * 2 + 8 + 16 * 2 * 2 + 16 + 16 * 2 + 4 + 4 * 4;
     ST(dev_alloc(ctx, ctx->d_wave, (size_t)cap * per + 64 * 256));
     char* p = (char*)ctx->d_wave.ptr;
     auto take = [&](size_t bytes) {
@@ -631,6 +656,10 @@ mcev_status ensure_wave(mcev_ctx* ctx) {
     w.sig = (uint32_t*)take(4 * cap);
     w.pflags = (uint32_t*)take(4 * cap);
     w.sh_c = (float*)take(4 * cap);
+    w.sh_g = (float*)take(4 * cap);
+    w.sh_m = (int32_t*)take(4 * cap);
+    w.Ltot = (float*)take(4 * cap);
+    w.delta = (float*)take(4 * cap);
     if (!ctx->d_counters.ptr) {
         ST(dev_alloc(ctx, ctx->d_counters, 64 * sizeof(int32_t)));
         CU(cudaMemsetAsync(ctx->d_counters.ptr, 0, 64 * sizeof(int32_t), ctx->stream));
@@ -672,7 +701,7 @@ mcev_status ensure_tcrit(mcev_ctx* ctx, float alpha, int variant, int spp_min, i
 }
 
 DevParams dev_params(const mcev_ctx* ctx, bool want_sig) {
-    DevParams P;
+    DevParams P{};
     P.width = ctx->W;
     P.height = ctx->H;
     P.max_depth = ctx->params.max_depth;
@@ -907,7 +936,7 @@ void mcev_destroy(mcev_ctx* ctx) {
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
-    DevBuf* bufs[] = {&ctx->d_nodes, &ctx->d_tris, &ctx->d_mats, &ctx->d_env, &ctx->d_marg, &ctx->d_cond,
+    DevBuf* bufs[] = {&ctx->d_nodes, &ctx->d_tris, &ctx->d_uv, &ctx->d_mats, &ctx->d_env, &ctx->d_marg, &ctx->d_cond,
                       &ctx->d_tpdf, &ctx->frames[0].buf, &ctx->frames[1].buf, &ctx->d_wave, &ctx->d_counters,
                       &ctx->d_pix, &ctx->d_tcrit, &ctx->d_jobs, &ctx->d_bqueue};
     for (DevBuf* b : bufs) dev_free(ctx, *b);
@@ -976,6 +1005,10 @@ mcev_status mcev_scene_upload(mcev_ctx* ctx, const mcev_scene_desc* s) {
             return fail(ctx, MCEV_ERR_ARG, "albedo outside [0,1] or negative emission");
     }
     if (s->env && (s->env_w <= 0 || s->env_h <= 0)) return fail(ctx, MCEV_ERR_ARG, "bad environment size");
+    if (s->mat_textured)
+        for (int m = 0; m < s->n_materials; ++m)
+            if (s->mat_textured[m] && s->mat_type[m] != MAT_DIFFUSE)
+                return fail(ctx, MCEV_ERR_ARG, "only Lambertian materials can be textured");
     if (s->env)
         for (int64_t i = 0; i < (int64_t)s->env_w * s->env_h; ++i)
             if (!(s->env[i] >= 0.0f) || !std::isfinite(s->env[i]))
@@ -985,6 +1018,14 @@ mcev_status mcev_scene_upload(mcev_ctx* ctx, const mcev_scene_desc* s) {
     ctx->ref_valid = false;
     ctx->vtx.resize(9 * (size_t)s->n_triangles);
     ctx->tri_mat.assign(s->tri_material, s->tri_material + s->n_triangles);
+    ctx->tri_uv.clear();
+    if (s->uvs) {
+        ctx->tri_uv.resize(6 * (size_t)s->n_triangles);
+        for (int64_t t = 0; t < s->n_triangles; ++t)
+            for (int c = 0; c < 3; ++c)
+                for (int a2 = 0; a2 < 2; ++a2)
+                    ctx->tri_uv[6 * t + 2 * c + a2] = s->uvs[2 * (int64_t)s->triangles[3 * t + c] + a2];
+    }
     for (int64_t t = 0; t < s->n_triangles; ++t)
         for (int c = 0; c < 3; ++c)
             for (int a = 0; a < 3; ++a) ctx->vtx[9 * t + 3 * c + a] = s->vertices[3 * (int64_t)s->triangles[3 * t + c] + a];
@@ -1021,7 +1062,7 @@ mcev_status mcev_scene_upload(mcev_ctx* ctx, const mcev_scene_desc* s) {
     }
     std::vector<float4> mats(s->n_materials);
     for (int m = 0; m < s->n_materials; ++m) {
-        int ty = s->mat_type[m];
+        int ty = s->mat_type[m] | ((s->mat_textured && s->mat_textured[m]) ? MAT_TEXTURED : 0);
         float tf;
         std::memcpy(&tf, &ty, 4);
         mats[m] = make_float4(tf, s->mat_albedo[m], s->mat_rough[m], s->mat_emit[m]);
@@ -1139,6 +1180,68 @@ mcev_status mcev_trace_samples(mcev_ctx* ctx, double t, const int32_t* pixels, i
     return MCEV_OK;
 }
 
+
+mcev_status mcev_set_texture(mcev_ctx* ctx, const float* texture, int32_t width, int32_t height) {
+    if (!ctx) return MCEV_ERR_ARG;
+    if (texture && (width < 1 || height < 1)) return fail(ctx, MCEV_ERR_ARG, "bad texture size");
+    ctx->dsc.tex = texture;
+    ctx->dsc.tex_w = texture ? width : 0;
+    ctx->dsc.tex_h = texture ? height : 0;
+    return MCEV_OK;
+}
+
+mcev_status mcev_set_emission(mcev_ctx* ctx, const float* emission, int32_t n_materials) {
+    if (!ctx) return MCEV_ERR_ARG;
+    if (emission && n_materials != ctx->n_mats)
+        return fail(ctx, MCEV_ERR_ARG, "emission has %d entries, the scene %d materials", n_materials, ctx->n_mats);
+    ctx->dsc.emit = emission;
+    return MCEV_OK;
+}
+
+mcev_status mcev_render_mean(mcev_ctx* ctx, double t, int32_t spp, float* mean_out) {
+    ST(check_ready(ctx));
+    if (spp < 1 || !mean_out) return fail(ctx, MCEV_ERR_ARG, "need spp >= 1 and mean_out");
+    reset_call_counters(ctx);
+    ST(frame_setup(ctx, t, 0));
+    StatsArgs A{};
+    A.cur = ctx->cur;
+    A.ref = ctx->ref;
+    A.mean_out = mean_out;
+    A.eps = ctx->params.eps;
+    A.spp_min = A.spp_batch = A.spp_max = spp;
+    A.mode = MODE_MEAN;
+    return run_rounds(ctx, ctx->frames[0], A, nullptr, nullptr);
+}
+
+mcev_status mcev_backward(mcev_ctx* ctx, double t, int32_t spp, const float* grad_mean, float* grad_texture,
+                          float* grad_emission) {
+    ST(check_ready(ctx));
+    if (spp < 1 || !grad_mean) return fail(ctx, MCEV_ERR_ARG, "need spp >= 1 and grad_mean");
+    if (grad_texture && !ctx->dsc.tex) return fail(ctx, MCEV_ERR_STATE, "no texture set");
+    reset_call_counters(ctx);
+    ST(frame_setup(ctx, t, 0));
+    const int64_t npix = (int64_t)ctx->W * ctx->H;
+    LAUNCH(MCEV_K_STATS, launch_iota(ctx->queue[0], npix, ctx->sms, ctx->stream));
+    const DevParams P = dev_params(ctx, false);
+    DevParams Padj = P;
+    Padj.adjoint = 1;
+    Padj.spp = spp;
+    Padj.grad_mean = grad_mean;
+    Padj.grad_tex = grad_texture;
+    Padj.grad_emit = grad_emission;
+    const int64_t per_chunk = std::max<int64_t>(1, ctx->wave.cap / spp);
+    for (int64_t j0 = 0; j0 < npix; j0 += per_chunk) {
+        const int64_t nj = std::min(per_chunk, npix - j0);
+        // pass 1: every path's radiance; pass 2: replay with the adjoint
+        ST(trace_chunk(ctx, ctx->frames[0], P, ctx->queue[0], j0, spp, 0, nj * spp, nullptr));
+        CU(cudaMemcpyAsync(ctx->wave.Ltot, ctx->wave.L, sizeof(float) * nj * spp, cudaMemcpyDeviceToDevice,
+                           ctx->stream));
+        ST(trace_chunk(ctx, ctx->frames[0], Padj, ctx->queue[0], j0, spp, 0, nj * spp, nullptr));
+    }
+    CU(cudaStreamSynchronize(ctx->stream));
+    ST(drain_events(ctx));
+    return MCEV_OK;
+}
 
 mcev_status mcev_render_events_batch(mcev_ctx* runner, const mcev_job* jobs, int32_t n_jobs, float C, float alpha,
                                      int32_t spp_batch, int32_t spp_max, mcev_stats* stats_out) {

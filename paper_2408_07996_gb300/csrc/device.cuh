@@ -191,6 +191,33 @@ __device__ __forceinline__ float power_heuristic(float a, float b) {
 
 __device__ __forceinline__ uint32_t fnv(uint32_t h, uint32_t w) { return (h ^ w) * 16777619u; }
 
+// ------------------------------------------------------------------ texture
+// Barycentric coordinates (b1, b2) of point p in triangle (a, b, c) from the
+// normal equations of p - a = b1 (b - a) + b2 (c - a).
+__device__ __forceinline__ void barycentric(f3 p, f3 a, f3 b, f3 c, float& b1, float& b2) {
+    const f3 e1 = b - a, e2 = c - a, vp = p - a;
+    const float d00 = dot3(e1, e1), d01 = dot3(e1, e2), d11 = dot3(e2, e2);
+    const float d20 = dot3(vp, e1), d21 = dot3(vp, e2);
+    const float den = d00 * d11 - d01 * d01;
+    b1 = (d11 * d20 - d01 * d21) / den;
+    b2 = (d00 * d21 - d01 * d20) / den;
+}
+
+// nearest texel of texture coordinates (u, v), wrapped to [0, 1)
+__device__ __forceinline__ int texel_of(const DevScene& sc, float u, float v) {
+    u -= floorf(u);
+    v -= floorf(v);
+    // the clamps also catch u = 1 after rounding and NaN coordinates (degenerate triangles)
+    const int ix = max(0, min((int)(u * (float)sc.tex_w), sc.tex_w - 1));
+    const int iy = max(0, min((int)(v * (float)sc.tex_h), sc.tex_h - 1));
+    return iy * sc.tex_w + ix;
+}
+
+// scalar albedo of an RGB texel: Rec. 709 luminance
+#define MCEV_Y_R 0.2126f
+#define MCEV_Y_G 0.7152f
+#define MCEV_Y_B 0.0722f
+
 // ------------------------------------------------------------------ intersection
 // Watertight test: the ray is sheared so it becomes the +z axis; 2D edge
 // functions U, V, W of the sheared vertices decide containment.

@@ -73,6 +73,11 @@ __global__ void __launch_bounds__(256) k_raygen(DevFrame fr, DevParams P, Wave w
         w.L[p] = 0.0f;
         w.pdf_prev[p] = 0.0f;
         w.pix_k[p] = make_int2(entry, (int)k);
+        if (Q.adjoint && Q.grad_mean) {
+            // d loss / d L of this path: d loss / d mean * d mean / d ln(L + eps) * d ln(L + eps) / dL
+            const float Lt = w.Ltot[p];
+            w.delta[p] = isfinite(Lt) ? __ldg(Q.grad_mean + pix) / ((float)Q.spp * (Lt + Q.eps)) : 0.0f;
+        }
         if (Q.want_sig) {
             w.sig[p] = FNV_BASIS;
             w.pflags[p] = NO_FLAGS;
@@ -157,7 +162,8 @@ __global__ void MCEV_SHADE_BOUNDS k_shade(DevScene sc, DevFrame fr, DevParams P,
         const f3 d = xyz(rd);
         bool cont = false, shadow = false;
         f3 P0 = mk3(0, 0, 0), wi_next = mk3(0, 0, 0), sh_dir = mk3(0, 0, 0);
-        float sh_tmax = 0.0f, sh_c = 0.0f;
+        float sh_tmax = 0.0f, sh_c = 0.0f, sh_g = 0.0f;
+        int sh_m = -1;
         if (inst < 0) {
             // miss: environment radiance (Sec. 3.1 samples the light reaching the pixel)
             if (Q.want_sig) sig = fnv(sig, 0xFFFFFFFFu);
@@ -193,8 +199,26 @@ __global__ void MCEV_SHADE_BOUNDS k_shade(DevScene sc, DevFrame fr, DevParams P,
             const f3 wo = d * -1.0f;
             const int mat = ovr >= 0 ? ovr : __float_as_int(q1.w);
             const float4 mv = __ldg(S.mats + mat);
-            const int type = __float_as_int(mv.x);
-            const float alb = mv.y, rough = mv.z, emit = mv.w;
+            const int tword = __float_as_int(mv.x);
+            const int type = tword & 0xFF;
+            float alb = mv.y;
+            const float rough = mv.z;
+            // the override applies to the scene's emitters only (NEE samples that fixed set)
+            const float emit = (S.emit && mv.w > 0.0f) ? __ldg(S.emit + mat) : mv.w;
+            int texel = -1;
+            if ((tword & MAT_TEXTURED) && S.tex && S.tri_uv) {
+                // albedo = luminance of the nearest texel at the hit's texture coordinates
+                float b1, b2;
+                barycentric(xf_point(i0, i1, i2, P0), xyz(q0), xyz(q1), xyz(q2), b1, b2);
+                const float b0 = 1.0f - b1 - b2;
+                const float2 t0 = __ldg(S.tri_uv + 3 * tri), t1 = __ldg(S.tri_uv + 3 * tri + 1),
+                             t2 = __ldg(S.tri_uv + 3 * tri + 2);
+                texel = texel_of(S, b0 * t0.x + b1 * t1.x + b2 * t2.x, b0 * t0.y + b1 * t1.y + b2 * t2.y);
+                const float* rgb = S.tex + 3 * (int64_t)texel;
+                alb = MCEV_Y_R * __ldg(rgb) + MCEV_Y_G * __ldg(rgb + 1) + MCEV_Y_B * __ldg(rgb + 2);
+                if (Q.want_sig) sig = fnv(sig, (uint32_t)texel);
+            }
+            const float dlt = Q.adjoint ? w.delta[p] : 0.0f;
             uint32_t flags = 0;
             const float cos_o = dot3(ng, wo);
             if (emit > 0.0f && cos_o > 0.0f) {
@@ -212,8 +236,17 @@ __global__ void MCEV_SHADE_BOUNDS k_shade(DevScene sc, DevFrame fr, DevParams P,
                     }
                 }
                 L += beta * wgt * emit;
+                if (Q.adjoint && Q.grad_emit) atomicAdd(Q.grad_emit + mat, dlt * beta * wgt);
             }
             if (depth < Q.max_depth && alb > 0.0f) {
+                // adjoint: every contribution after this vertex carries one factor of its albedo
+                if (Q.adjoint && texel >= 0 && Q.grad_tex && dlt != 0.0f) {
+                    const float g = dlt * (w.Ltot[p] - L) / alb;
+                    float* gt = Q.grad_tex + 3 * (int64_t)texel;
+                    atomicAdd(gt, g * MCEV_Y_R);
+                    atomicAdd(gt + 1, g * MCEV_Y_G);
+                    atomicAdd(gt + 2, g * MCEV_Y_B);
+                }
                 const f3 nn = cos_o < 0.0f ? ng * -1.0f : ng;
                 f3 tb, bt;
                 onb(nn, tb, bt);
@@ -226,6 +259,7 @@ __global__ void MCEV_SHADE_BOUNDS k_shade(DevScene sc, DevFrame fr, DevParams P,
                     const bool use_env = S.env_ok && (F.n_lights == 0 || u01(x.x) < 0.5f);
                     f3 wi = mk3(0, 0, 0);
                     float pl = 0.0f, Le = 0.0f, tmax = __int_as_float(0x7f800000);
+                    int lmat = -1;
                     if (use_env) {
                         float pdf;
                         wi = env_sample(S, u01(x.z), u01(x.w), pdf, Le);
@@ -244,7 +278,8 @@ __global__ void MCEV_SHADE_BOUNDS k_shade(DevScene sc, DevFrame fr, DevParams P,
                         const float cl = -dot3(xyz(an), wi);
                         if (cl > 0.0f) {
                             pl = F.p_area / ((float)F.n_lights * a1.w) * dist * dist / cl;
-                            Le = a0.w;
+                            lmat = __float_as_int(a2.w);
+                            Le = S.emit ? __ldg(S.emit + lmat) : a0.w;
                         }
                         tmax = dist - Q.t_min;
                     }
@@ -256,6 +291,8 @@ __global__ void MCEV_SHADE_BOUNDS k_shade(DevScene sc, DevFrame fr, DevParams P,
                             flags |= 2u;
                             const float wgt = Q.mis ? power_heuristic(pl, pb) : 1.0f;
                             sh_c = beta * f * wil.z * Le * wgt / pl;
+                            sh_g = beta * f * wil.z * wgt / pl;
+                            sh_m = lmat;
                             sh_dir = wi;
                             sh_tmax = tmax;
                             shadow = true;
@@ -288,6 +325,10 @@ __global__ void MCEV_SHADE_BOUNDS k_shade(DevScene sc, DevFrame fr, DevParams P,
             w.sh_o[si] = make_float4(P0.x, P0.y, P0.z, __int_as_float(p));
             w.sh_d[si] = make_float4(sh_dir.x, sh_dir.y, sh_dir.z, sh_tmax);
             w.sh_c[si] = sh_c;
+            if (Q.adjoint) {
+                w.sh_g[si] = sh_g;
+                w.sh_m[si] = sh_m;
+            }
         }
         const int ni = warp_append(w.counters + (1 - cur), cont);
         if (cont) {
@@ -317,6 +358,7 @@ __global__ void MCEV_TRAV_BOUNDS k_shadow(DevScene sc, DevFrame fr, DevParams P,
         if (!occluded(S, F, xyz(o), xyz(d), Q.t_min, d.w, &e, work)) {
             w.L[p] += w.sh_c[i];
             if (Q.want_sig) w.pflags[p] |= 4u;
+            if (Q.adjoint && Q.grad_emit && w.sh_m[i] >= 0) atomicAdd(Q.grad_emit + w.sh_m[i], w.delta[p] * w.sh_g[i]);
         }
     }
     if (e) atomicOr(err, 1);
@@ -440,7 +482,10 @@ __global__ void __launch_bounds__(256) k_stats(Wave w, StatsArgs A0, const int32
         A.cur.mean[pix] = c.mean;
         A.cur.m2[pix] = c.m2;
         if (!detect) {
-            if (n >= A.spp_max) {
+            if (n >= A.spp_max && A.mode == MODE_MEAN) {
+                A.mean_out[pix] = c.mean;
+                if (A.spp_out) A.spp_out[pix] = n;
+            } else if (n >= A.spp_max) {
                 A.ref.n[pix] = n;
                 A.ref.mean[pix] = c.mean;
                 A.ref.m2[pix] = c.m2;

@@ -7,7 +7,7 @@
 
 namespace mcev {
 
-enum { MODE_REFERENCE = 0, MODE_DETECT = 1 };
+enum { MODE_REFERENCE = 0, MODE_DETECT = 1, MODE_MEAN = 2 };
 enum { VAR_ONE_TAILED = 0, VAR_TWO_TAILED = 1, VAR_MEAN_ONLY = 2, VAR_UNIFORM = 3 };
 enum { SE_PAPER = 0, SE_WELCH = 1 };
 

@@ -15,7 +15,7 @@
 //   BVH whose triangles carry their instance id and resolved material.
 //   Instance record (112 B): M rows 0..2, Minv rows 0..2 (3x4 each, float4),
 //   then (blas root node, material override, instance id or -1, 0).
-//   Light (64 B): v0.xyz|Le, v1.xyz|area, v2.xyz|0, n.xyz|0 (world space).
+//   Light (64 B): v0.xyz|Le, v1.xyz|area, v2.xyz|material, n.xyz|0 (world space).
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -45,6 +45,8 @@ struct Node {
 };
 
 enum { MAT_DIFFUSE = 0, MAT_GGX = 1 };
+// material type word: low byte = BSDF, bit 8 = albedo from the texture
+enum { MAT_TEXTURED = 0x100 };
 
 struct DevScene {
     const Node* nodes;        // BLAS nodes of every mesh
@@ -57,6 +59,10 @@ struct DevScene {
     int32_t env_w, env_h;
     int32_t env_ok;           // environment present with positive total radiance
     int32_t has_env;          // environment present (lookups on miss)
+    const float2* tri_uv;     // 3 texture coordinates per triangle (leaf order), or null
+    const float* tex;         // caller's RGB albedo texture [tex_h][tex_w][3], or null
+    int32_t tex_w, tex_h;
+    const float* emit;        // caller's emitted radiance per material (overrides the table), or null
 };
 
 struct DevFrame {
@@ -79,6 +85,12 @@ struct DevParams {
     float eps;
     float t_min;
     int32_t want_sig;         // maintain the decision signature
+    // adjoint replay (mcev_backward): 1 in the second pass over a chunk
+    int32_t adjoint;
+    int32_t spp;              // samples per pixel of the replayed frame
+    const float* grad_mean;   // d loss / d mean ln(L + eps), per pixel
+    float* grad_tex;          // accumulated d loss / d texel RGB
+    float* grad_emit;         // accumulated d loss / d emitted radiance, per material
 };
 
 // Wavefront buffers of one chunk (capacity = `cap` paths).
@@ -98,6 +110,10 @@ struct Wave {
     float4* sh_o;             // xyz origin, w = path slot
     float4* sh_d;             // xyz direction, w = t_max
     float* sh_c;              // unoccluded contribution
+    float* sh_g;              // adjoint: contribution / emitted radiance of the sampled light
+    int32_t* sh_m;            // adjoint: material of the sampled light (-1: environment)
+    float* Ltot;              // adjoint: radiance of each path from the first pass
+    float* delta;             // adjoint: d loss / d L of each path
     // device counters: [0],[1] ray queue sizes, [2] shadow count, [3] pixel queue
     // size, [4] non-finite path values, [5] events +, [6] events -, [7] at cap
     int32_t* counters;
