@@ -2,7 +2,7 @@
 
 This package only *generates inputs*: triangle meshes, per-triangle and
 per-instance materials, camera and instance keyframes, and environment-map
-texels.  It holds none of the method's arithmetic (no ray tracing, no
+texels, and event videos for the quality metrics.  It holds none of the method's arithmetic (no ray tracing, no
 statistics, no sampling of paths).  Every function is deterministic in its
 `seed` argument.
 """
@@ -16,6 +16,7 @@ from .procedural import (  # noqa: F401
     batch_workloads,
     cornell_box,
     empty_env,
+    event_video_pair,
     furnace_sphere,
     icosphere_field,
     plane_under_env,

@@ -642,3 +642,42 @@ def batch_workloads(n_jobs: int = 64, seed: int = 20240818) -> list:
         w.t_min = 1e-4 * _bbox_diag(sc)
         jobs.append(w)
     return jobs
+
+
+def event_video_pair(width: int, height: int, frames: int, seed: int = 20240820, move: float = 0.05,
+                     drop: float = 0.03, flip: float = 0.01, noise: float = 2e-4):
+    """Two int8 event videos [frames, height, width] of {-1, 0, +1} for the
+    quality metrics: `a` holds the events of a drifting sinusoidal grating
+    seen by an ideal log sensor (a pixel fires when its level index
+    floor(4 * I) changes between frames, polarity = sign of the change),
+    `b` is `a` with each event moved by one lattice step (probability
+    `move`), dropped (`drop`) or flipped (`flip`), plus spurious events at
+    rate `noise` per voxel."""
+    rng = np.random.default_rng(seed)
+    y, x = np.mgrid[0:height, 0:width].astype(np.float64)
+    kx, ky = rng.uniform(0.02, 0.08, 2)
+    vx, vy = rng.uniform(0.3, 1.5, 2)
+    levels = []
+    for t in range(frames + 1):
+        I = 0.5 + 0.25 * np.sin(kx * (x - vx * t)) + 0.25 * np.sin(ky * (y - vy * t) + 0.3 * np.sin(0.05 * x))
+        levels.append(np.floor(4.0 * I))
+    lv = np.stack(levels)
+    a = np.sign(lv[1:] - lv[:-1]).astype(np.int8)
+    b = np.zeros_like(a)
+    t, r, c = np.nonzero(a)
+    pol = a[t, r, c]
+    u = rng.random(t.size)
+    keep = u >= drop
+    moved = (u >= drop) & (u < drop + move)
+    axis = rng.integers(0, 3, t.size)
+    step = rng.choice(np.array([-1, 1]), t.size)
+    t2, r2, c2 = t.copy(), r.copy(), c.copy()
+    t2[moved & (axis == 0)] += step[moved & (axis == 0)]
+    r2[moved & (axis == 1)] += step[moved & (axis == 1)]
+    c2[moved & (axis == 2)] += step[moved & (axis == 2)]
+    ok = keep & (t2 >= 0) & (t2 < frames) & (r2 >= 0) & (r2 < height) & (c2 >= 0) & (c2 < width)
+    fl = rng.random(t.size) < flip
+    b[t2[ok], r2[ok], c2[ok]] = np.where(fl[ok], -pol[ok], pol[ok])
+    spur = rng.random(a.shape) < noise
+    b[spur] = rng.choice(np.array([-1, 1], np.int8), int(spur.sum()))
+    return a, b
