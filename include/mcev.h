@@ -350,6 +350,55 @@ typedef struct {
  * would not fit the fixed scratch); MCEV_ERR_CUDA for failed CUDA calls. */
 mcev_status mcev_detect_batch_static(const mcev_detect_args* args, int64_t* n_undecided);
 
+/* ------------------------------------------------------------------------
+ * Quality metrics of event videos (Sec. 4.2)
+ *
+ * The paper scores an event video against the uniform-sampling baseline by
+ * the RMSE and PSNR of its event frames (negative / no / positive event
+ * stored as 0 / 0.5 / 1) and by an F1 score and a chamfer distance ("PSCD")
+ * of signed point clouds, one point (x, y, t) with its polarity per event,
+ * where only points of equal polarity are compared.  The thresholds behind
+ * the last two are not given; these are this library's definitions:
+ *   - coordinates are lattice units (pixel column, pixel row, frame index);
+ *   - d(a, B) = Euclidean distance from a to the nearest point of B with a's
+ *     polarity, or the lattice diagonal D = sqrt((W-1)^2+(H-1)^2+(T-1)^2)
+ *     when B has no point of that polarity;
+ *   - a point is matched when d^2 <= tau2; precision = matched a / |A|,
+ *     recall = matched b / |B| (1 for an empty cloud), F1 = 2PR/(P+R);
+ *   - PSCD = (mean_a d(a, B) + mean_b d(b, A)) / (2 D);
+ *   - MSE over all W*H*T mapped values, RMSE = sqrt(MSE),
+ *     PSNR = -10 log10(MSE) (HUGE_VAL for identical videos).
+ * The distances are exact (integer distance transform on the GPU).
+ * ------------------------------------------------------------------------ */
+typedef struct mcev_quality {
+    int64_t voxels;       /* W * H * T */
+    int64_t n_a, n_b;     /* events in a, in b */
+    int64_t matched_a;    /* events of a with d^2 <= tau2 */
+    int64_t matched_b;
+    int64_t none_a;       /* events of a whose polarity b lacks (d = D) */
+    int64_t none_b;
+    int64_t sq_diff;      /* sum over voxels of (a - b)^2 on the raw values */
+    double sum_dist_a;    /* sum over a's events of d(a, B), lattice units */
+    double sum_dist_b;
+    double diag;          /* D */
+    double rmse, psnr, precision, recall, f1, pscd;
+    float gpu_ms;         /* device time of the call */
+    int32_t kernel_launches;
+} mcev_quality;
+
+/* Metrics of event video `a` against `b`: device int8 arrays
+ * [frames][height][width] of {-1, 0, +1} (caller-owned, read only).
+ * tau2: squared match radius in lattice units (3: the 26 neighbours).
+ * d2_a / d2_b: optional device int32 [frames*height*width] receiving, at each
+ * event voxel of a (of b), the squared distance d^2 to the other video's
+ * nearest same-polarity event, -2 where it has none, and -1 at voxels
+ * without an event; NULL to skip.  Results go to *out (host).  The context
+ * needs no scene; scratch of 8 bytes per voxel is allocated through it.
+ * Errors: ARG (NULL inputs, an extent outside 1..16384, tau2 < 0, a value
+ * outside {-1, 0, 1}), OOM, CUDA. */
+mcev_status mcev_event_quality(mcev_ctx* ctx, const int8_t* a, const int8_t* b, int32_t width, int32_t height,
+                               int32_t frames, int32_t tau2, int32_t* d2_a, int32_t* d2_b, mcev_quality* out);
+
 #ifdef __cplusplus
 }
 #endif

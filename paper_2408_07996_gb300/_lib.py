@@ -85,6 +85,19 @@ class DetectArgs(C.Structure):
     ]
 
 
+class Quality(C.Structure):
+    _fields_ = [
+        ("voxels", C.c_int64), ("n_a", C.c_int64), ("n_b", C.c_int64), ("matched_a", C.c_int64),
+        ("matched_b", C.c_int64), ("none_a", C.c_int64), ("none_b", C.c_int64), ("sq_diff", C.c_int64),
+        ("sum_dist_a", C.c_double), ("sum_dist_b", C.c_double), ("diag", C.c_double),
+        ("rmse", C.c_double), ("psnr", C.c_double), ("precision", C.c_double), ("recall", C.c_double),
+        ("f1", C.c_double), ("pscd", C.c_double), ("gpu_ms", C.c_float), ("kernel_launches", C.c_int32),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 # every symbol include/mcev.h declares, with its ctypes signature
 SIGNATURES = {
     "mcev_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int32, C.c_int32]),
@@ -102,6 +115,8 @@ SIGNATURES = {
     "mcev_set_emission": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
     "mcev_render_mean": (C.c_int, [C.c_void_p, C.c_double, C.c_int32, C.c_void_p]),
     "mcev_backward": (C.c_int, [C.c_void_p, C.c_double, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mcev_event_quality": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32,
+                                     C.c_int32, C.c_void_p, C.c_void_p, C.POINTER(Quality)]),
     "mcev_render_events_batch": (C.c_int, [C.c_void_p, C.POINTER(JobDesc), C.c_int32, C.c_float, C.c_float,
                                            C.c_int32, C.c_int32, C.POINTER(Stats)]),
     "mcev_trace_samples": (C.c_int, [C.c_void_p, C.c_double, C.c_void_p, C.c_int64, C.c_int64, C.c_int32,

@@ -267,6 +267,43 @@ def render_events_batch(runner: Renderer, jobs, C_: float, alpha: float, spp_bat
     return outs, (st.as_dict() if stats else None)
 
 
+def event_quality(a: torch.Tensor, b: torch.Tensor, tau2: int = 3, want_d2: bool = False,
+                  runner: "Renderer | None" = None) -> dict:
+    """RMSE, PSNR, polarity-aware F1 and chamfer distance of event video
+    `a` against `b` (int8 [T, H, W] or [H, W] of {-1, 0, 1} on the device),
+    computed by mcev_event_quality.  `runner`: a context to run on (its
+    stream and allocator); by default one cached per device.  With
+    `want_d2`, also the per-voxel squared distances d2_a, d2_b."""
+    assert a.shape == b.shape and a.dtype == torch.int8 and b.dtype == torch.int8 and a.is_cuda and b.is_cuda
+    shp = (1,) * (3 - a.dim()) + tuple(a.shape)
+    T, H, W = shp
+    if runner is None:
+        runner = _quality_ctx(a.device)
+    a = a.contiguous()
+    b = b.contiguous()
+    d2a = torch.empty(shp, dtype=torch.int32, device=a.device) if want_d2 else None
+    d2b = torch.empty(shp, dtype=torch.int32, device=a.device) if want_d2 else None
+    q = L.Quality()
+    L.check(runner.lib.mcev_event_quality(runner.ctx, _tptr(a), _tptr(b), W, H, T, int(tau2), _tptr(d2a), _tptr(d2b),
+                                          C.byref(q)), runner.ctx, "mcev_event_quality")
+    out = q.as_dict()
+    if want_d2:
+        out["d2_a"], out["d2_b"] = d2a, d2b
+    return out
+
+
+_QCTX: dict = {}
+
+
+def _quality_ctx(device: torch.device) -> "Renderer":
+    idx = device.index if device.index is not None else torch.cuda.current_device()
+    r = _QCTX.get(idx)
+    if r is None:
+        r = _QCTX[idx] = Renderer(1, 1, idx)
+    r.set_stream(torch.cuda.current_stream(r.device))
+    return r
+
+
 class EventFrames(torch.autograd.Function):
     """(texture, emission) -> per-pixel mean ln(L + eps) at t0 and t1.
 

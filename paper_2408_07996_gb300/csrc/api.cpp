@@ -18,6 +18,7 @@
 #include "../../include/mcev.h"
 #include "bvh.h"
 #include "kernels.h"
+#include "quality.h"
 #include "layout.h"
 #include "tdist.h"
 
@@ -90,6 +91,7 @@ struct mcev_ctx {
     float static_lo[3], static_hi[3];
 
     // device scene
+    DevBuf d_quality;                       // event-quality scratch: two int32 volumes + accumulators
     DevBuf d_nodes, d_tris, d_uv, d_mats, d_env, d_marg, d_cond, d_tpdf;
     DevScene dsc{};
     Frame frames[2];
@@ -938,7 +940,7 @@ void mcev_destroy(mcev_ctx* ctx) {
     cudaStreamSynchronize(ctx->stream);
     DevBuf* bufs[] = {&ctx->d_nodes, &ctx->d_tris, &ctx->d_uv, &ctx->d_mats, &ctx->d_env, &ctx->d_marg, &ctx->d_cond,
                       &ctx->d_tpdf, &ctx->frames[0].buf, &ctx->frames[1].buf, &ctx->d_wave, &ctx->d_counters,
-                      &ctx->d_pix, &ctx->d_tcrit, &ctx->d_jobs, &ctx->d_bqueue};
+                      &ctx->d_pix, &ctx->d_tcrit, &ctx->d_jobs, &ctx->d_bqueue, &ctx->d_quality};
     for (DevBuf* b : bufs) dev_free(ctx, *b);
     for (cudaEvent_t e : ctx->evpool) cudaEventDestroy(e);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
@@ -1409,3 +1411,74 @@ mcev_status mcev_set_state(mcev_ctx* ctx, const void* dev_buf, size_t bytes) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ event-video quality (Sec. 4.2)
+mcev_status mcev_event_quality(mcev_ctx* ctx, const int8_t* a, const int8_t* b, int32_t width, int32_t height,
+                               int32_t frames, int32_t tau2, int32_t* d2_a, int32_t* d2_b, mcev_quality* out) {
+    if (!ctx) return MCEV_ERR_ARG;
+    if (!a || !b || !out) return fail(ctx, MCEV_ERR_ARG, "need a, b and out");
+    const int32_t mx = QUALITY_MAX_EXTENT;
+    if (width < 1 || height < 1 || frames < 1 || width > mx || height > mx || frames > mx)
+        return fail(ctx, MCEV_ERR_ARG, "extents must lie in 1..%d", mx);
+    if (tau2 < 0) return fail(ctx, MCEV_ERR_ARG, "tau2 must be >= 0");
+    CU(cudaSetDevice(ctx->device));
+    const int64_t n = (int64_t)width * height * frames;
+    const size_t vol = ((size_t)n * sizeof(int32_t) + 255) & ~size_t(255);
+    ST(dev_alloc(ctx, ctx->d_quality, 2 * vol + QACC_WORDS * sizeof(unsigned long long)));
+    char* base = (char*)ctx->d_quality.ptr;
+    QualityArgs A{};
+    A.a = a;
+    A.b = b;
+    A.W = width;
+    A.H = height;
+    A.T = frames;
+    A.tau2 = tau2;
+    A.d2_a = d2_a;
+    A.d2_b = d2_b;
+    A.vol0 = (int32_t*)base;
+    A.vol1 = (int32_t*)(base + vol);
+    A.acc = (unsigned long long*)(base + 2 * vol);
+    int nl = 0;
+    CU(cudaEventRecord(ctx->ev0, ctx->stream));
+    CU(launch_quality(A, ctx->sms, ctx->stream, &nl));
+    CU(cudaEventRecord(ctx->ev1, ctx->stream));
+    unsigned long long acc[QACC_WORDS];
+    CU(cudaMemcpyAsync(acc, A.acc, sizeof acc, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    ctx->d2h += (int64_t)sizeof acc;
+    if (acc[QACC_BAD]) return fail(ctx, MCEV_ERR_ARG, "event values must be -1, 0 or +1");
+    float ms = 0.0f;
+    CU(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
+    mcev_quality q{};
+    q.voxels = n;
+    q.n_a = (int64_t)acc[QACC_NA];
+    q.n_b = (int64_t)acc[QACC_NB];
+    q.matched_a = (int64_t)acc[QACC_MATCH_A];
+    q.matched_b = (int64_t)acc[QACC_MATCH_B];
+    q.none_a = (int64_t)acc[QACC_NONE_A];
+    q.none_b = (int64_t)acc[QACC_NONE_B];
+    q.sq_diff = (int64_t)acc[QACC_SQ];
+    double sa, sb;
+    std::memcpy(&sa, &acc[QACC_SUM_A], sizeof sa);
+    std::memcpy(&sb, &acc[QACC_SUM_B], sizeof sb);
+    const double D = std::sqrt((double)(width - 1) * (width - 1) + (double)(height - 1) * (height - 1) +
+                               (double)(frames - 1) * (frames - 1));
+    q.diag = D;
+    q.sum_dist_a = sa + (double)q.none_a * D;
+    q.sum_dist_b = sb + (double)q.none_b * D;
+    // frames mapped {-1, 0, 1} -> {0, 0.5, 1}: each unit of (a - b)^2 is 1/4
+    const double mse = (double)q.sq_diff / (4.0 * (double)n);
+    q.rmse = std::sqrt(mse);
+    q.psnr = mse == 0.0 ? HUGE_VAL : -10.0 * std::log10(mse);
+    q.precision = q.n_a ? (double)q.matched_a / (double)q.n_a : 1.0;
+    q.recall = q.n_b ? (double)q.matched_b / (double)q.n_b : 1.0;
+    q.f1 = q.precision + q.recall > 0.0 ? 2.0 * q.precision * q.recall / (q.precision + q.recall) : 0.0;
+    const double ma = q.n_a ? q.sum_dist_a / (double)q.n_a : 0.0;
+    const double mb = q.n_b ? q.sum_dist_b / (double)q.n_b : 0.0;
+    q.pscd = D > 0.0 ? (ma + mb) / (2.0 * D) : 0.0;
+    q.gpu_ms = ms;
+    q.kernel_launches = nl;
+    ctx->launches += nl;
+    *out = q;
+    return MCEV_OK;
+}

@@ -1,0 +1,42 @@
+// quality.h -- launchers of the event-video quality kernels (Sec. 4.2 metrics).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mcev {
+
+// accumulator slots (unsigned 64-bit words; the distance sums are doubles)
+enum {
+    QACC_SQ = 0,        // sum over voxels of (a - b)^2
+    QACC_NA = 1,        // events in a
+    QACC_NB = 2,        // events in b
+    QACC_BAD = 3,       // nonzero if a value outside {-1, 0, 1} was seen
+    QACC_MATCH_A = 4,   // a events within sqrt(tau2) of a same-polarity b event
+    QACC_NONE_A = 5,    // a events whose polarity b lacks entirely
+    QACC_SUM_A = 6,     // double: sum of distances of the other a events
+    QACC_MATCH_B = 7,
+    QACC_NONE_B = 8,
+    QACC_SUM_B = 9,
+    QACC_WORDS = 16
+};
+
+struct QualityArgs {
+    const int8_t* a;
+    const int8_t* b;
+    int32_t W, H, T;
+    int32_t tau2;
+    int32_t* d2_a;               // optional per-voxel squared distances of a's events (else NULL)
+    int32_t* d2_b;
+    int32_t* vol0;               // scratch volumes, W*H*T int32 each
+    int32_t* vol1;
+    unsigned long long* acc;     // QACC_WORDS words
+};
+
+// Largest extent per axis: keeps every squared lattice distance below 2^30.
+constexpr int32_t QUALITY_MAX_EXTENT = 16384;
+
+// Enqueues every kernel on `st`; returns the first launch error.  `launches`
+// receives the number of kernels enqueued.
+cudaError_t launch_quality(const QualityArgs& A, int sms, cudaStream_t st, int* launches);
+
+}  // namespace mcev

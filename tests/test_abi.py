@@ -31,7 +31,7 @@ def test_struct_layouts_match_header(tmp_path):
     # ask the C compiler for sizeof/offsetof of every field the binding uses
     import subprocess
     structs = {"mcev_params": L.Params, "mcev_stats": L.Stats, "mcev_scene_desc": L.SceneDesc,
-               "mcev_detect_args": L.DetectArgs}
+               "mcev_detect_args": L.DetectArgs, "mcev_quality": L.Quality}
     lines = []
     for cname, cls in structs.items():
         lines.append(f'printf("{cname} %zu\\n", sizeof({cname}));')
