@@ -40,6 +40,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="terrain720p")
+    ap.add_argument("--dims", type=int, nargs=3, default=None, metavar=("W", "H", "T"),
+                    help="video size of --workload quality (default 1280 720 100)")
     ap.add_argument("--no-uniform", action="store_true")
     ap.add_argument("--no-matched", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -302,7 +304,13 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
-QUALITY_BYTES_PER_VOXEL = 106   # frame error 2 + 4 x (rows 1+4, y 4+4, t 4+4, match 1+4)
+# algorithmic bytes of one mcev_event_quality call: per voxel the frame error
+# reads 2, and each of the 4 transforms (2 directions x 2 polarities) reads
+# its video (1) and writes 4 in the row pass, reads 4 and writes 4 in each
+# column pass, and reads the query video (1) in the match pass; per event,
+# the match pass reads its 4-byte distance
+QUALITY_BYTES_PER_VOXEL = 2 + 4 * (1 + 4 + 8 + 8 + 1)
+QUALITY_BYTES_PER_EVENT = 4
 
 
 def _hbm_peak():
@@ -327,7 +335,7 @@ def run_quality(args):
     import scenegen as sg
     from paper_2408_07996_gb300.api import event_quality
 
-    T, H, W = 100, 720, 1280
+    W, H, T = args.dims or (1280, 720, 100)
     a_np, b_np = sg.event_video_pair(W, H, T, seed=20240820)
     a = torch.from_numpy(a_np).cuda()
     b = torch.from_numpy(b_np).cuda()
@@ -347,18 +355,20 @@ def run_quality(args):
     gpu_ms = sum(r["gpu_ms"] for r in res) / K
     n = T * H * W
     peak, basis = _hbm_peak()
-    achieved = QUALITY_BYTES_PER_VOXEL * n / (gpu_ms / 1e3) / 1e9
     q = res[-1]
+    algo_bytes = QUALITY_BYTES_PER_VOXEL * n + QUALITY_BYTES_PER_EVENT * (q["n_a"] + q["n_b"])
+    achieved = algo_bytes / (gpu_ms / 1e3) / 1e9
     line = {"metric": "event-video quality metrics (RMSE, PSNR, F1, PSCD) throughput", "value": n * K / (ms / 1e3) / 1e9,
             "unit": "Gvoxels/s", "n_gpus": 1, "steps": K, "warmup": Wm, "ms_per_step": ms / K,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": "quality_1280x720x100", "width": W, "height": H, "frames": T, "tau2": 3,
+            "config": {"workload": f"quality_{W}x{H}x{T}", "width": W, "height": H, "frames": T, "tau2": 3,
                        "events_a": q["n_a"], "events_b": q["n_b"],
                        "l2": "two int32 scratch volumes of 369 MB each are streamed every step (> L2)"},
             "gpu_launches": sum(r["kernel_launches"] for r in res),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None, "basis": basis,
-                         "bytes_per_voxel": QUALITY_BYTES_PER_VOXEL, "avg_call_ms": gpu_ms},
+                         "bytes_per_call": algo_bytes, "bytes_per_voxel": QUALITY_BYTES_PER_VOXEL,
+                         "bytes_per_event": QUALITY_BYTES_PER_EVENT, "avg_call_ms": gpu_ms},
             "metrics": {k: q[k] for k in ("rmse", "psnr", "precision", "recall", "f1", "pscd")},
             "clocks": clk}
     print(json.dumps(line), flush=True)

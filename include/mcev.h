@@ -393,7 +393,8 @@ typedef struct mcev_quality {
  * event voxel of a (of b), the squared distance d^2 to the other video's
  * nearest same-polarity event, -2 where it has none, and -1 at voxels
  * without an event; NULL to skip.  Results go to *out (host).  The context
- * needs no scene; scratch of 8 bytes per voxel is allocated through it.
+ * needs no scene; scratch (8 bytes per voxel, plus up to 2 GiB of envelope
+ * stacks) is allocated through it.
  * Errors: ARG (NULL inputs, an extent outside 1..16384, tau2 < 0, a value
  * outside {-1, 0, 1}), OOM, CUDA. */
 mcev_status mcev_event_quality(mcev_ctx* ctx, const int8_t* a, const int8_t* b, int32_t width, int32_t height,

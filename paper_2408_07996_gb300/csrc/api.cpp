@@ -1424,7 +1424,8 @@ mcev_status mcev_event_quality(mcev_ctx* ctx, const int8_t* a, const int8_t* b, 
     CU(cudaSetDevice(ctx->device));
     const int64_t n = (int64_t)width * height * frames;
     const size_t vol = ((size_t)n * sizeof(int32_t) + 255) & ~size_t(255);
-    ST(dev_alloc(ctx, ctx->d_quality, 2 * vol + QACC_WORDS * sizeof(unsigned long long)));
+    const size_t stk = ((size_t)quality_stack_bytes(width, height, frames, ctx->sms) + 255) & ~size_t(255);
+    ST(dev_alloc(ctx, ctx->d_quality, 2 * vol + stk + QACC_WORDS * sizeof(unsigned long long)));
     char* base = (char*)ctx->d_quality.ptr;
     QualityArgs A{};
     A.a = a;
@@ -1437,15 +1438,17 @@ mcev_status mcev_event_quality(mcev_ctx* ctx, const int8_t* a, const int8_t* b, 
     A.d2_b = d2_b;
     A.vol0 = (int32_t*)base;
     A.vol1 = (int32_t*)(base + vol);
-    A.acc = (unsigned long long*)(base + 2 * vol);
+    A.stack = base + 2 * vol;
+    A.acc = (unsigned long long*)(base + 2 * vol + stk);
     int nl = 0;
     CU(cudaEventRecord(ctx->ev0, ctx->stream));
     CU(launch_quality(A, ctx->sms, ctx->stream, &nl));
     CU(cudaEventRecord(ctx->ev1, ctx->stream));
-    unsigned long long acc[QACC_WORDS];
-    CU(cudaMemcpyAsync(acc, A.acc, sizeof acc, cudaMemcpyDeviceToHost, ctx->stream));
+    std::vector<unsigned long long> acc(QACC_WORDS);
+    CU(cudaMemcpyAsync(acc.data(), A.acc, QACC_WORDS * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                       ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
-    ctx->d2h += (int64_t)sizeof acc;
+    ctx->d2h += (int64_t)(QACC_WORDS * sizeof(unsigned long long));
     if (acc[QACC_BAD]) return fail(ctx, MCEV_ERR_ARG, "event values must be -1, 0 or +1");
     float ms = 0.0f;
     CU(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
@@ -1464,6 +1467,11 @@ mcev_status mcev_event_quality(mcev_ctx* ctx, const int8_t* a, const int8_t* b, 
     const double D = std::sqrt((double)(width - 1) * (width - 1) + (double)(height - 1) * (height - 1) +
                                (double)(frames - 1) * (frames - 1));
     q.diag = D;
+    // distances of d^2 < QHIST come as counts per value
+    for (int v = 1; v < QHIST; ++v) {
+        sa += (double)acc[QACC_HIST_A + v] * std::sqrt((double)v);
+        sb += (double)acc[QACC_HIST_B + v] * std::sqrt((double)v);
+    }
     q.sum_dist_a = sa + (double)q.none_a * D;
     q.sum_dist_b = sb + (double)q.none_b * D;
     // frames mapped {-1, 0, 1} -> {0, 0.5, 1}: each unit of (a - b)^2 is 1/4

@@ -12,8 +12,8 @@
 //     in one forward sweep with integer separation points
 //     floor((u^2 - i^2 + F(u) - F(i)) / (2 (u - i))) and read back in one
 //     backward sweep (Meijster, Roerdink and Hesselink 2000; Felzenszwalb
-//     and Huttenlocher 2012).  One thread owns one line; its envelope lives
-//     in shared memory.  All arithmetic is integer, so the result is exact.
+//     and Huttenlocher 2012).  One thread owns one line at a time.  All
+//     arithmetic is integer, so the result is exact.
 #include <algorithm>
 #include <climits>
 #include <utility>
@@ -25,12 +25,7 @@ namespace {
 
 constexpr int32_t QINF = 1 << 30;
 constexpr int QBLOCK = 256;
-constexpr int SMEM_BUDGET = 200 * 1024;
-
-__device__ __forceinline__ int64_t floordiv(int64_t a, int64_t b) {  // b > 0
-    const int64_t q = a / b;
-    return (a % b != 0 && a < 0) ? q - 1 : q;
-}
+constexpr int SMEM_BUDGET = 220 * 1024;
 
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
@@ -154,59 +149,82 @@ __global__ void k_edt_rows(const int8_t* __restrict__ v, int W, int64_t rows, in
 }
 
 // ---------------------------------------------------------------- columns: lower envelope of parabolas
+constexpr int COL_PREFETCH = 16;
+
+__device__ __forceinline__ int32_t floordiv32(int32_t a, int32_t b) {  // b > 0
+    const int32_t q = a / b;
+    return (a % b != 0 && a < 0) ? q - 1 : q;
+}
+
 // Line `line` = (outer, inner x): elements base + u * step, u = 0..L-1,
-// base = outer * outer_stride + x.  Shared layout per thread tid, entry k:
-// site s[k], start t[k] (int16), site value fs[k] (int32), all [k][nt].
-__global__ void k_edt_cols(const int32_t* __restrict__ in, int32_t* __restrict__ out, int64_t n_lines, int W,
-                           int64_t outer_stride, int64_t step, int L) {
-    extern __shared__ int32_t q_env[];
-    const int nt = blockDim.x, tid = threadIdx.x;
-    int32_t* fs = q_env;                                          // [L][nt]
-    int16_t* s = reinterpret_cast<int16_t*>(q_env + (size_t)L * nt);   // [L][nt]
-    int16_t* t = s + (size_t)L * nt;                              // [L][nt]
-    for (int64_t line = (int64_t)blockIdx.x * nt + tid; line < n_lines; line += (int64_t)gridDim.x * nt) {
+// base = outer * outer_stride + x.  The envelope is a stack of sites (site s,
+// interval start t, site value f); its top lives in registers, the entries
+// below it in global memory, entry (depth k, thread g) at k * G + g for the
+// G threads of the launch, packed as (s | t << 16, f).  A thread owns one
+// stack and walks lines g, g + G, ...; keeping the stacks out of shared
+// memory lets every SM run at full occupancy, which hides the latency of the
+// sweeps (stacks in shared memory held a 720-long line pass to 39 threads
+// per SM and ran 6.7x slower).  The forward sweep loads 16 elements ahead.
+// Every quantity fits in int32: extents <= 16384 keep squared distances
+// <= 3 * 16383^2 < 2^30.
+__global__ void __launch_bounds__(256) k_edt_cols(const int32_t* __restrict__ in, int32_t* __restrict__ out,
+                                                    int64_t n_lines, int W, int64_t outer_stride, int64_t step, int L,
+                                                    int2* __restrict__ stack) {
+    const int64_t G = (int64_t)gridDim.x * blockDim.x;
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int64_t line = g; line < n_lines; line += G) {
         const int64_t x = line % W, outer = line / W;
         const int32_t* src = in + outer * outer_stride + x;
         int32_t* dst = out + outer * outer_stride + x;
-        int q = -1;
-        for (int u = 0; u < L; ++u) {
-            const int32_t fu = __ldg(src + (int64_t)u * step);
-            if (fu >= QINF) continue;
-            while (q >= 0) {
-                const int k = q * nt + tid;
-                const int64_t tq = t[k], sq = s[k];
-                const int64_t f_site = (tq - sq) * (tq - sq) + fs[k];
-                const int64_t f_new = (tq - u) * (tq - u) + fu;
-                if (f_site > f_new) --q;
-                else break;
-            }
-            if (q < 0) {
-                q = 0;
-                s[tid] = (int16_t)u;
-                t[tid] = 0;
-                fs[tid] = fu;
-            } else {
-                const int k = q * nt + tid;
-                const int64_t i = s[k];
-                const int64_t num = (int64_t)u * u - i * i + fu - fs[k];
-                const int64_t w = 1 + floordiv(num, 2 * ((int64_t)u - i));
-                if (w < L) {
-                    ++q;
-                    const int k2 = q * nt + tid;
-                    s[k2] = (int16_t)u;
-                    t[k2] = (int16_t)w;
-                    fs[k2] = fu;
+        int depth = 0;
+        int32_t top_s = 0, top_t = 0, top_f = 0;
+        for (int u0 = 0; u0 < L; u0 += COL_PREFETCH) {
+            int32_t buf[COL_PREFETCH];
+#pragma unroll
+            for (int j = 0; j < COL_PREFETCH; ++j)
+                buf[j] = u0 + j < L ? __ldg(src + (int64_t)(u0 + j) * step) : QINF;
+#pragma unroll
+            for (int j = 0; j < COL_PREFETCH; ++j) {
+                const int32_t u = u0 + j, fu = buf[j];
+                if (fu >= QINF) continue;
+                while (depth > 0) {
+                    const int32_t f_site = (top_t - top_s) * (top_t - top_s) + top_f;
+                    const int32_t f_new = (top_t - u) * (top_t - u) + fu;
+                    if (f_site <= f_new) break;
+                    if (--depth > 0) {
+                        const int2 e = stack[(int64_t)(depth - 1) * G + g];
+                        top_s = e.x & 0xFFFF;
+                        top_t = (int32_t)((uint32_t)e.x >> 16);
+                        top_f = e.y;
+                    }
+                }
+                if (depth == 0) {
+                    depth = 1;
+                    top_s = u;
+                    top_t = 0;
+                    top_f = fu;
+                } else {
+                    const int32_t w = 1 + floordiv32(u * u - top_s * top_s + fu - top_f, 2 * (u - top_s));
+                    if (w < L) {
+                        stack[(int64_t)(depth - 1) * G + g] = make_int2(top_s | (top_t << 16), top_f);
+                        ++depth;
+                        top_s = u;
+                        top_t = w;
+                        top_f = fu;
+                    }
                 }
             }
         }
-        for (int u = L - 1; u >= 0; --u) {
+        for (int32_t u = L - 1; u >= 0; --u) {
             int32_t d = QINF;
-            if (q >= 0) {
-                const int k = q * nt + tid;
-                const int64_t sq = s[k];
-                const int64_t f = ((int64_t)u - sq) * ((int64_t)u - sq) + fs[k];
-                d = (int32_t)(f < QINF ? f : QINF);
-                if (u == t[k]) --q;
+            if (depth > 0) {
+                d = (u - top_s) * (u - top_s) + top_f;
+                if (u == top_t && --depth > 0) {
+                    const int2 e = stack[(int64_t)(depth - 1) * G + g];
+                    top_s = e.x & 0xFFFF;
+                    top_t = (int32_t)((uint32_t)e.x >> 16);
+                    top_f = e.y;
+                }
             }
             dst[(int64_t)u * step] = d;
         }
@@ -214,25 +232,67 @@ __global__ void k_edt_cols(const int32_t* __restrict__ in, int32_t* __restrict__
 }
 
 // ---------------------------------------------------------------- matching of one polarity
+__device__ __forceinline__ void match_one(int32_t d, int64_t i, int32_t* d2_out, int tau2, uint32_t* hist,
+                                          unsigned long long& matched, unsigned long long& none, double& sum) {
+    if (d >= QINF) {
+        ++none;
+        if (d2_out) d2_out[i] = -2;
+    } else {
+        matched += d <= tau2;
+        if (d >= QHIST) sum += sqrt((double)d);
+        else if (d > 0) atomicAdd(hist + d, 1u);
+        if (d2_out) d2_out[i] = d;
+    }
+}
+
+// vec: the query video is 4-byte aligned (the distance volume always is), so
+// each thread takes 4 voxels per step with one 4-byte and one 16-byte load.
+// Distances are tallied per squared value in a shared histogram.
 __global__ void __launch_bounds__(QBLOCK) k_match(const int8_t* __restrict__ qv, const int32_t* __restrict__ d2,
-                                                  int64_t n, int pol, int tau2, int32_t* __restrict__ d2_out,
-                                                  unsigned long long* acc, int slot) {
+                                                  int64_t n, int pol, int tau2, int vec, int32_t* __restrict__ d2_out,
+                                                  unsigned long long* acc, int slot, unsigned long long* ghist) {
+    __shared__ uint32_t hist[QHIST];
+    for (int b = threadIdx.x; b < QHIST; b += blockDim.x) hist[b] = 0;
+    __syncthreads();
     unsigned long long matched = 0, none = 0;
     double sum = 0.0;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t nth = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += nth) {
-        if (qv[i] != pol) continue;
-        const int32_t d = __ldg(d2 + i);
-        if (d >= QINF) {
-            ++none;
-            if (d2_out) d2_out[i] = -2;
-        } else {
-            matched += d <= tau2;
-            sum += sqrt((double)d);
-            if (d2_out) d2_out[i] = d;
+    int64_t done = 0;
+    if (vec) {
+        const int64_t n4 = n >> 2;
+        const int32_t* q4 = reinterpret_cast<const int32_t*>(qv);
+        const int4* d4 = reinterpret_cast<const int4*>(d2);
+        for (int64_t i = tid; i < n4; i += nth) {
+            const int32_t qw = __ldg(q4 + i);
+            if (qw == 0) continue;      // no event among the 4 voxels
+            bool any = false;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) any |= (int)(int8_t)(qw >> (8 * k)) == pol;
+            if (!any) continue;
+            const int4 dv = __ldg(d4 + i);
+            const int32_t ds[4] = {dv.x, dv.y, dv.z, dv.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if ((int)(int8_t)(qw >> (8 * k)) == pol)
+                    match_one(ds[k], 4 * i + k, d2_out, tau2, hist, matched, none, sum);
         }
+        done = n4 << 2;
     }
-    block_flush(matched, none, 0ull, sum, acc, slot, slot + 1, -1, slot + 2);
+    for (int64_t i = done + tid; i < n; i += nth)
+        if (qv[i] == pol) match_one(__ldg(d2 + i), i, d2_out, tau2, hist, matched, none, sum);
+    block_flush(matched, none, 0ull, sum, acc, slot, slot + 1, -1, slot + 2);   // synchronises the block
+    for (int b = threadIdx.x; b < QHIST; b += blockDim.x)
+        if (hist[b]) atomicAdd(ghist + b, (unsigned long long)hist[b]);
+}
+
+// Blocks of 256 threads for the column kernel: enough for every line, at
+// most 8 per SM, and no more than the stack scratch holds.
+int stack_blocks(int64_t n_lines, int L, int sms) {
+    const int64_t by_lines = (n_lines + 255) / 256;
+    const int64_t by_sms = (int64_t)sms * 8;
+    const int64_t by_mem = QUALITY_STACK_BYTES / (8 * (int64_t)L * 256);
+    return (int)std::max<int64_t>(1, std::min(by_lines, std::min(by_sms, by_mem)));
 }
 
 int grid_of(int64_t work, int per_block, int sms, int per_sm) {
@@ -243,6 +303,17 @@ int grid_of(int64_t work, int per_block, int sms, int per_sm) {
 
 }  // namespace
 
+int64_t quality_stack_bytes(int32_t W, int32_t H, int32_t T, int sms) {
+    const int64_t lines[2] = {(int64_t)T * W, (int64_t)H * W}, len[2] = {H, T};
+    int64_t need = 0;
+    for (int ax = 0; ax < 2; ++ax) {
+        if (len[ax] < 2) continue;
+        const int b = stack_blocks(lines[ax], (int)len[ax], sms);
+        need = std::max<int64_t>(need, (int64_t)b * 256 * len[ax] * 8);
+    }
+    return need;
+}
+
 cudaError_t launch_quality(const QualityArgs& A, int sms, cudaStream_t st, int* launches) {
     static bool attrs[64] = {};
     int dev = 0;
@@ -250,9 +321,7 @@ cudaError_t launch_quality(const QualityArgs& A, int sms, cudaStream_t st, int* 
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64 || !attrs[dev]) {
         if ((e = cudaFuncSetAttribute(k_edt_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BUDGET)) !=
-                cudaSuccess ||
-            (e = cudaFuncSetAttribute(k_edt_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BUDGET)) !=
-                cudaSuccess)
+            cudaSuccess)
             return e;
         if (dev >= 0 && dev < 64) attrs[dev] = true;
     }
@@ -269,7 +338,7 @@ cudaError_t launch_quality(const QualityArgs& A, int sms, cudaStream_t st, int* 
     const int wpb = (int)std::max<int64_t>(1, std::min<int64_t>(8, SMEM_BUDGET / (4 * W)));
     auto cols_threads = [](int64_t L) {
         int64_t nt = SMEM_BUDGET / (8 * L);
-        nt = nt >= 32 ? (nt / 32) * 32 : nt;
+        nt = nt >= 64 ? (nt / 32) * 32 : nt;
         return (int)std::max<int64_t>(1, std::min<int64_t>(256, nt));
     };
     for (int dir = 0; dir < 2; ++dir) {
@@ -283,21 +352,21 @@ cudaError_t launch_quality(const QualityArgs& A, int sms, cudaStream_t st, int* 
             k_edt_rows<<<grid_of(H * T, wpb, sms, 16), 32 * wpb, (size_t)wpb * W * 4, st>>>(target, (int)W, H * T,
                                                                                             pol, cur);
             ++nl;
-            if (H > 1) {
-                const int nt = cols_threads(H);
-                k_edt_cols<<<grid_of(T * W, nt, sms, 64), nt, (size_t)nt * H * 8, st>>>(cur, other, T * W, (int)W,
-                                                                                         H * W, W, (int)H);
+            // column passes along y, then t
+            const int64_t lines[2] = {T * W, H * W}, ostride[2] = {H * W, W}, stp[2] = {W, H * W};
+            const int64_t len[2] = {H, T};
+            for (int ax = 0; ax < 2; ++ax) {
+                if (len[ax] < 2) continue;
+                const int L = (int)len[ax];
+                const int blocks = stack_blocks(lines[ax], L, sms);
+                k_edt_cols<<<blocks, 256, 0, st>>>(cur, other, lines[ax], (int)W, ostride[ax], stp[ax], L,
+                                                    reinterpret_cast<int2*>(A.stack));
                 ++nl;
                 std::swap(cur, other);
             }
-            if (T > 1) {
-                const int nt = cols_threads(T);
-                k_edt_cols<<<grid_of(H * W, nt, sms, 64), nt, (size_t)nt * T * 8, st>>>(cur, other, H * W, (int)W, W,
-                                                                                         H * W, (int)T);
-                ++nl;
-                std::swap(cur, other);
-            }
-            k_match<<<grid_of(n, QBLOCK, sms, 8), QBLOCK, 0, st>>>(query, cur, n, pol, A.tau2, d2_out, A.acc, slot);
+            const int qvec = (reinterpret_cast<uintptr_t>(query) & 3) == 0;
+            k_match<<<grid_of(n / 4 + 1, QBLOCK, sms, 8), QBLOCK, 0, st>>>(
+                query, cur, n, pol, A.tau2, qvec, d2_out, A.acc, slot, A.acc + (dir ? QACC_HIST_B : QACC_HIST_A));
             ++nl;
         }
     }

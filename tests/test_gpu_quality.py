@@ -50,7 +50,9 @@ def _compare(a, b, tau2=3):
 
 
 @pytest.mark.parametrize("shape,seed", [((10, 64, 96), 1), ((7, 33, 70), 2), ((1, 45, 61), 3), ((5, 1, 200), 4),
-                                        ((12, 40, 1), 5), ((3, 130, 257), 6)])
+                                        ((12, 40, 1), 5), ((3, 130, 257), 6),
+                                        # long columns and many frames
+                                        ((2, 300, 40), 7), ((260, 8, 12), 8)])
 def test_quality_parity(shape, seed):
     T, H, W = shape
     a, b = sg.event_video_pair(W, H, T, seed=seed, move=0.1, noise=1e-3)
