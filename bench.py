@@ -310,6 +310,12 @@ def run_batch(args):
 # column pass, and reads the query video (1) in the match pass; per event,
 # the match pass reads its 4-byte distance
 QUALITY_BYTES_PER_VOXEL = 2 + 4 * (1 + 4 + 8 + 8 + 1)
+# statistics kernel (a7-a10 fused): per pixel visit it reads the queue entry
+# (4), the running and reference (n, mean, M2) (24) and writes the running
+# state (12) and a re-queue entry or event/spp (4); per path it reads one
+# 4-byte radiance
+STATS_BYTES_PER_PIXEL_VISIT = 44
+STATS_BYTES_PER_PATH = 4
 QUALITY_BYTES_PER_EVENT = 4
 
 
@@ -372,6 +378,35 @@ def run_quality(args):
             "metrics": {k: q[k] for k in ("rmse", "psnr", "precision", "recall", "f1", "pscd")},
             "clocks": clk}
     print(json.dumps(line), flush=True)
+
+
+def traversal_l1_peak(local: int) -> dict:
+    """Node visits per second of the closest-hit kernel when every node and
+    triangle fetch hits L1: camera inside a closed level-3 icosphere (1,280
+    triangles; BVH + triangles ~80 KB), diffuse bounces to depth 6 so that
+    rays are as incoherent as the terrain's, 1280x720 x 32 uniform samples.
+    Best of 3 frames; the measured ceiling of the traversal loop."""
+    import scenegen as sg
+    from paper_2408_07996_gb300 import UNIFORM
+    from paper_2408_07996_gb300.api import Renderer
+
+    sc = sg.furnace_sphere(0.5, 1.0, level=3)
+    w = sg.Workload("l1_sphere", sc, 1280, 720, [0.0, 1.0], spp_min=32, spp_batch=32, spp_max=32, C=0.2,
+                    alpha=0.05, max_depth=6, nee=0, mis=0)
+    r = Renderer(1280, 720, local)
+    r.upload(w.scene)
+    r.configure(w)
+    r.set_params(variant=UNIFORM, profile=1)
+    best = None
+    for _ in range(3):
+        st = r.render_events(w.times[0], w.times[1], w.C, w.alpha, 32, 32)["stats"]
+        rate = st["nodes_closest"] / (st["kernel_ms"][1] / 1e3)
+        if best is None or rate > best["node_visits_per_s"]:
+            best = {"node_visits_per_s": rate, "rays_per_s": st["rays_closest"] / (st["kernel_ms"][1] / 1e3),
+                    "nodes_per_ray": st["nodes_closest"] / max(1, st["rays_closest"]),
+                    "tris_per_ray": st["tris_closest"] / max(1, st["rays_closest"])}
+    r.close()
+    return best
 
 
 # ------------------------------------------------------------------ our arm
@@ -479,13 +514,27 @@ def main():
                                  for i, n in enumerate(["raygen", "extend", "shade", "shadow", "stats"])},
                 "peak_basis": f"{sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_max_mhz:.0f} MHz"}
 
+    # statistics kernel against HBM
+    hbm_peak, hbm_basis = _hbm_peak()
+    stats_bytes = STATS_BYTES_PER_PIXEL_VISIT * sum(s["stats_pixels"] for s in steps) + STATS_BYTES_PER_PATH * paths
+    roof_stats = {"kernel": "k_stats (log, batch statistics, t-test, re-queue, events)", "bound": "hbm",
+                  "achieved": stats_bytes / (kms[4] / 1e3) / 1e9 if kms[4] else None, "peak": hbm_peak,
+                  "unit": "GB/s", "basis": hbm_basis,
+                  "frac": stats_bytes / (kms[4] / 1e3) / 1e9 / hbm_peak if kms[4] else None,
+                  "bytes_per_frame": stats_bytes / K, "avg_launch_ms": kms[4] / max(1, kcnt[4])}
+    if rank == 0 and not args.no_uniform:
+        pk = traversal_l1_peak(local)
+        roofline["l1_peak"] = {**pk, "scene": "inside a 1,280-triangle icosphere (BVH in L1), depth 6, 1280x720 x 32 spp"}
+        roofline["node_visits_per_s"] = nodes / (ext_ms / 1e3) if ext_ms else None
+        roofline["frac_of_l1_peak"] = roofline["node_visits_per_s"] / pk["node_visits_per_s"] if ext_ms else None
+
     line = {"metric": METRIC, "value": frames_per_s, "unit": "event frames/s", "n_gpus": world, "steps": K,
             "warmup": Wm, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": _config(w),
             "mpaths_per_s": mpaths, "paths_per_frame": paths / K,
             "mean_spp": paths / K / (H * Wd),
             "events_per_frame": sum(s["events_pos"] + s["events_neg"] for s in steps) / K,
-            "gpu_launches": launches, "roofline": roofline, "clocks": clk}
+            "gpu_launches": launches, "roofline": roofline, "roofline_stats": roof_stats, "clocks": clk}
 
     # uniform-spp comparator on the same GPU, same frame pair and reference
     if not args.no_uniform and rank == 0:

@@ -139,6 +139,7 @@ typedef struct {
     int32_t reserved;
     double kernel_ms[MCEV_K_CLASSES];
     int64_t h2d_bytes, d2h_bytes;   /* host<->device copies made by the call */
+    int64_t stats_pixels;   /* pixel visits of the statistics kernel (sum over its launches) */
 } mcev_stats;
 
 /* Creates a context on CUDA device `device` for width x height images.

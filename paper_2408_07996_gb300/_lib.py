@@ -54,7 +54,7 @@ class Stats(C.Structure):
         ("nodes_closest", C.c_int64), ("tris_closest", C.c_int64), ("nodes_shadow", C.c_int64),
         ("tris_shadow", C.c_int64), ("rays_closest", C.c_int64), ("rays_shadow", C.c_int64),
         ("kernel_count", C.c_int32 * 5), ("reserved", C.c_int32), ("kernel_ms", C.c_double * 5),
-        ("h2d_bytes", C.c_int64), ("d2h_bytes", C.c_int64),
+        ("h2d_bytes", C.c_int64), ("d2h_bytes", C.c_int64), ("stats_pixels", C.c_int64),
     ]
 
     def as_dict(self):

@@ -61,6 +61,7 @@ struct mcev_ctx {
     int32_t kcount[MCEV_K_CLASSES] = {0};
     double kms[MCEV_K_CLASSES] = {0};
     int64_t h2d = 0, d2h = 0;
+    int64_t stats_pix = 0;                  // pixel visits of k_stats in the current call
     // profile mode: event pairs around launches, drained at round ends
     std::vector<cudaEvent_t> evpool;
     std::vector<int> evclass;
@@ -634,7 +635,9 @@ mcev_status frame_setup(mcev_ctx* ctx, double t, int slot) {
 mcev_status ensure_wave(mcev_ctx* ctx) {
     const int64_t cap = ctx->params.wavefront > 0 ? ctx->params.wavefront : ((int64_t)1 << 25);
     if (ctx->d_wave.ptr && ctx->wave.cap == cap) return MCEV_OK;
-    const size_t per = 4 * 3 + 4 * 2 + 8 + 16 * 2 * 2 + 16 + 16 * 2 + 4 + 4 * 4;
+    // path slots: L, sig, pflags, pix_k, Ltot, delta; per ray-queue slot (x2):
+    // ray_o, ray_d, ray_s; hit; shadow: sh_o, sh_d, sh_c, sh_g, sh_m
+    const size_t per = 4 + 4 + 4 + 8 + 4 + 4 + 2 * (16 + 16 + 16) + 16 + 16 + 16 + 4 + 4 + 4;
     ST(dev_alloc(ctx, ctx->d_wave, (size_t)cap * per + 64 * 256));
     char* p = (char*)ctx->d_wave.ptr;
     auto take = [&](size_t bytes) {
@@ -648,13 +651,13 @@ mcev_status ensure_wave(mcev_ctx* ctx) {
     w.ray_o[1] = (float4*)take(16 * cap);
     w.ray_d[0] = (float4*)take(16 * cap);
     w.ray_d[1] = (float4*)take(16 * cap);
+    w.ray_s[0] = (float4*)take(16 * cap);
+    w.ray_s[1] = (float4*)take(16 * cap);
     w.hit = (float4*)take(16 * cap);
     w.sh_o = (float4*)take(16 * cap);
     w.sh_d = (float4*)take(16 * cap);
     w.pix_k = (int2*)take(8 * cap);
-    w.beta = (float*)take(4 * cap);
     w.L = (float*)take(4 * cap);
-    w.pdf_prev = (float*)take(4 * cap);
     w.sig = (uint32_t*)take(4 * cap);
     w.pflags = (uint32_t*)take(4 * cap);
     w.sh_c = (float*)take(4 * cap);
@@ -803,6 +806,7 @@ mcev_status run_rounds(mcev_ctx* ctx, const Frame& fr, StatsArgs A, int64_t* pat
             const int64_t nj = std::min(per_chunk, Q - j0);
             ST(trace_chunk(ctx, fr, P, queue[qi], j0, spp_r, n_done, nj * spp_r, B));
             LAUNCH(MCEV_K_STATS, launch_stats(ctx->wave, A, queue[qi], j0, nj, queue[qi ^ 1], ctx->sms, ctx->stream, jobs));
+            ctx->stats_pix += nj;
         }
         paths += Q * spp_r;
         n_done += spp_r;
@@ -828,6 +832,7 @@ void reset_call_counters(mcev_ctx* ctx) {
         ctx->kms[i] = 0.0;
     }
     ctx->h2d = ctx->d2h = 0;
+    ctx->stats_pix = 0;
     ctx->evused = 0;
 }
 
@@ -862,6 +867,7 @@ mcev_status fill_stats(mcev_ctx* ctx, mcev_stats* stats_out, int64_t paths, int6
         stats_out->kernel_ms[i] = ctx->kms[i];
     }
     stats_out->h2d_bytes = ctx->h2d;
+    stats_out->stats_pixels = ctx->stats_pix;
     stats_out->d2h_bytes = ctx->d2h;
     if (c[15]) return fail(ctx, MCEV_ERR_STATE, "traversal stack overflow");
     return MCEV_OK;

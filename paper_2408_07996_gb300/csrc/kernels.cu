@@ -69,10 +69,9 @@ __global__ void __launch_bounds__(256) k_raygen(DevFrame fr, DevParams P, Wave w
                                F.fwd[2] + fx * F.right[2] + fy * F.up[2]));
         w.ray_o[cur][p] = make_float4(F.eye[0], F.eye[1], F.eye[2], __int_as_float((int)p));
         w.ray_d[cur][p] = make_float4(d.x, d.y, d.z, __int_as_float(job << 8));
-        w.beta[p] = 1.0f;
         w.L[p] = 0.0f;
-        w.pdf_prev[p] = 0.0f;
         w.pix_k[p] = make_int2(entry, (int)k);
+        w.ray_s[cur][p] = make_float4(1.0f, 0.0f, __int_as_float(entry), __int_as_float((int)k));
         if (Q.adjoint && Q.grad_mean) {
             // d loss / d L of this path: d loss / d mean * d mean / d ln(L + eps) * d ln(L + eps) / dL
             const float Lt = w.Ltot[p];
@@ -150,9 +149,11 @@ __global__ void MCEV_SHADE_BOUNDS k_shade(DevScene sc, DevFrame fr, DevParams P,
         const DevParams& Q = kBatch ? jobs[job].P : P;
         const float4 hv = w.hit[i];
         const int inst = __float_as_int(hv.y);
-        float beta = w.beta[p];
+        const float4 rs = w.ray_s[cur][i];
+        float beta = rs.x;
         float L = w.L[p];
-        const float pdf_prev = w.pdf_prev[p];
+        const float pdf_prev = rs.y;
+        float pdf_next = 0.0f;
         uint32_t sig = 0, pflags = NO_FLAGS;
         if (Q.want_sig) {
             sig = w.sig[p];
@@ -251,8 +252,8 @@ __global__ void MCEV_SHADE_BOUNDS k_shade(DevScene sc, DevFrame fr, DevParams P,
                 f3 tb, bt;
                 onb(nn, tb, bt);
                 const f3 wol = mk3(dot3(wo, tb), dot3(wo, bt), dot3(wo, nn));
-                const int2 pkv = w.pix_k[p];
-                const uint2 pk = make_uint2(kBatch ? ((uint32_t)pkv.x & 0xFFFFFFu) : (uint32_t)pkv.x, (uint32_t)pkv.y);
+                const uint32_t ent = (uint32_t)__float_as_int(rs.z);
+                const uint2 pk = make_uint2(kBatch ? (ent & 0xFFFFFFu) : ent, (uint32_t)__float_as_int(rs.w));
                 // next-event estimation
                 if (Q.nee && (S.env_ok || F.n_lights > 0)) {
                     const uint4 x = philox4x32_10(make_uint4(pk.x, pk.y, (uint32_t)(depth + 1), 0u), F.key0, F.key1);
@@ -307,7 +308,7 @@ __global__ void MCEV_SHADE_BOUNDS k_shade(DevScene sc, DevFrame fr, DevParams P,
                 if (f > 0.0f && pb > 0.0f && wil.z > 0.0f) {
                     flags |= 8u;
                     beta *= f * wil.z / pb;
-                    w.pdf_prev[p] = pb;
+                    pdf_next = pb;
                     wi_next = norm3(tb * wil.x + bt * wil.y + nn * wil.z);
                     cont = true;
                 }
@@ -315,7 +316,6 @@ __global__ void MCEV_SHADE_BOUNDS k_shade(DevScene sc, DevFrame fr, DevParams P,
             pflags = flags;
         }
         w.L[p] = L;
-        w.beta[p] = beta;
         if (Q.want_sig) {
             w.sig[p] = sig;
             w.pflags[p] = pflags;
@@ -334,6 +334,7 @@ __global__ void MCEV_SHADE_BOUNDS k_shade(DevScene sc, DevFrame fr, DevParams P,
         if (cont) {
             w.ray_o[1 - cur][ni] = make_float4(P0.x, P0.y, P0.z, __int_as_float(p));
             w.ray_d[1 - cur][ni] = make_float4(wi_next.x, wi_next.y, wi_next.z, __int_as_float((depth + 1) | (job << 8)));
+            w.ray_s[1 - cur][ni] = make_float4(beta, pdf_next, rs.z, rs.w);
         }
     }
 }
@@ -384,6 +385,17 @@ __device__ __forceinline__ Moments chan(Moments a, Moments b) {
 
 // kChecked: caller-supplied pixel ids and counts are range-checked (the
 // allocation-free entry point); the renderer's own queues use <false>.
+// log of a path value: the fast hardware logarithm by default (its error,
+// ~1e-7 absolute near 1, is far below the statistics' own noise)
+#ifndef MCEV_FAST_LOG
+#define MCEV_FAST_LOG 1
+#endif
+#if MCEV_FAST_LOG
+#define MCEV_LOG(x) __logf(x)
+#else
+#define MCEV_LOG(x) logf(x)
+#endif
+
 template <bool kChecked, bool kBatch>
 __global__ void __launch_bounds__(256) k_stats(Wave w, StatsArgs A0, const int32_t* __restrict__ queue, int64_t j0,
                                                int64_t n_pix, int32_t* __restrict__ next_queue,
@@ -427,19 +439,28 @@ __global__ void __launch_bounds__(256) k_stats(Wave w, StatsArgs A0, const int32
         const float* Lp = w.L + j * A.spp_r;
         for (int s0 = 0; s0 < A.spp_r && !decided; s0 += A.sub) {
             const int s1 = min(s0 + A.sub, A.spp_r);
-            // per-lane Welford over the lane's samples of this batch
+            // per-lane moments of the lane's samples of this batch, from sums
+            // shifted by the lane's first sample (no division per sample)
             Moments m{0.0f, 0.0f, 0.0f};
+            float y0 = 0.0f, s1d = 0.0f, s2d = 0.0f;
+            int cnt = 0;
             for (int s = s0 + lane; s < s1; s += 32) {
                 float Lv = Lp[s];
                 if (!isfinite(Lv)) {
                     Lv = 0.0f;
                     ++bad;
                 }
-                const float y = logf(Lv + A.eps);
-                m.n += 1.0f;
-                const float dl = y - m.mean;
-                m.mean += dl / m.n;
-                m.m2 += dl * (y - m.mean);
+                const float y = MCEV_LOG(Lv + A.eps);
+                if (cnt == 0) y0 = y;
+                const float d = y - y0;
+                s1d += d;
+                s2d = fmaf(d, d, s2d);
+                ++cnt;
+            }
+            if (cnt > 0) {
+                const float fn = (float)cnt;
+                const float md = s1d / fn;
+                m = Moments{fn, y0 + md, fmaxf(s2d - s1d * md, 0.0f)};
             }
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) {

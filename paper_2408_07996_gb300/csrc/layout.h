@@ -96,15 +96,15 @@ struct DevParams {
 // Wavefront buffers of one chunk (capacity = `cap` paths).
 struct Wave {
     // per path slot p
-    float* beta;
     float* L;
-    float* pdf_prev;
     uint32_t* sig;
     uint32_t* pflags;         // pending flags of the last vertex (0xFFFFFFFF = none)
     int2* pix_k;              // (pixel, sample index)
     // ray queues (ping-pong) and hits, per queue slot
     float4* ray_o[2];         // xyz origin, w = path slot (int bits)
     float4* ray_d[2];         // xyz direction, w = depth (int bits)
+    float4* ray_s[2];         // path state carried with the ray: throughput, pdf of the sampled
+                              // direction, queue entry and sample index (int bits)
     float4* hit;              // t, instance, leaf-order triangle, 0   (inst < 0: miss)
     // shadow rays
     float4* sh_o;             // xyz origin, w = path slot
