@@ -287,6 +287,14 @@ def test_terrain_full_frame_sampled_pixels(terrain):
     st = out["stats"]
     assert st["ref_paths"] == w.width * w.height * w.spp_max
     assert st["samples_used"] == int(n.sum()) and st["paths"] >= st["samples_used"]
+    # properties of Alg. 1 over every pixel: sample counts lie on the test
+    # schedule; a pixel that stopped early passed the one-tailed test, so its
+    # gap is below C and it cannot fire; every event pixel ran to the cap
+    on_schedule = ((n - w.spp_min) % w.spp_batch == 0) & (n >= w.spp_min) | (n == w.spp_max)
+    assert on_schedule.all() and n.max() <= w.spp_max
+    assert (n[ev != 0] == w.spp_max).all()
+    assert st["events_pos"] == int((ev > 0).sum()) and st["events_neg"] == int((ev < 0).sum())
+    assert st["pixels_at_cap"] == int((n == w.spp_max).sum())
     r.close()
 
 
