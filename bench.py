@@ -40,6 +40,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="terrain720p")
+    ap.add_argument("--frames", type=int, default=5, help="video length of --workload ablation")
     ap.add_argument("--dims", type=int, nargs=3, default=None, metavar=("W", "H", "T"),
                     help="video size of --workload quality (default 1280 720 100)")
     ap.add_argument("--no-uniform", action="store_true")
@@ -409,6 +410,55 @@ def traversal_l1_peak(local: int) -> dict:
     return best
 
 
+def run_ablation(args):
+    """The paper's comparison (Sec. 4.2, Table 2) on the terrain workload: a
+    short event video (frames t_3 -> t_{3+F}) rendered from the same
+    reference by the uniform-spp baseline and by each detector variant
+    (one-tailed t-test = the paper's method, mean-only and two-tailed
+    ablations, Welch standard error), each scored against the uniform video
+    with the Sec. 4.2 metrics and timed per frame."""
+    import torch
+
+    import scenegen as sg
+    from paper_2408_07996_gb300 import MEAN_ONLY, ONE_TAILED, SE_WELCH, TWO_TAILED, UNIFORM
+    from paper_2408_07996_gb300.api import Renderer, event_quality
+
+    w = sg.workload(args.workload if args.workload != "ablation" else "terrain720p")
+    F = args.frames
+    k0 = 3
+    r = Renderer(w.width, w.height, 0)
+    r.upload(w.scene)
+    r.configure(w)
+    r.render_reference(w.times[k0], w.spp_max)     # Alg. 1 first frame at t_{k0}
+    state = r.get_state().clone()
+
+    def video(variant, se_mode=0):
+        r.set_params(variant=variant, se_mode=se_mode)
+        r.set_state(state)
+        ev, ms, spp = [], 0.0, 0
+        for k in range(k0, k0 + F):
+            out = r.render_events(w.times[k], w.times[k + 1], w.C, w.alpha, w.spp_batch, w.spp_max)
+            ev.append(out["events"].clone())
+            ms += out["stats"]["gpu_ms"]
+            spp += out["stats"]["samples_used"]
+        return torch.stack(ev), ms / F, spp / F / (w.width * w.height)
+
+    uni, uni_ms, _ = video(UNIFORM)
+    rows = [{"method": "uniform", "ms_per_frame": uni_ms, "mean_spp": float(w.spp_max)}]
+    for name, var, se in (("one-tailed t-test (paper)", ONE_TAILED, 0), ("mean only", MEAN_ONLY, 0),
+                          ("two-tailed t-test", TWO_TAILED, 0), ("one-tailed, Welch SE", ONE_TAILED, SE_WELCH)):
+        v, ms, spp = video(var, se)
+        q = event_quality(v, uni)
+        rows.append({"method": name, "ms_per_frame": ms, "speedup": uni_ms / ms, "mean_spp": spp,
+                     "event_error_pct": 100.0 * float((v != uni).float().mean()),
+                     **{k: q[k] for k in ("rmse", "psnr", "f1", "pscd", "precision", "recall")}})
+        print(f"[ablation] {name}: {ms:.0f} ms/frame, F1 {q['f1']:.5f}", file=sys.stderr, flush=True)
+    r.close()
+    print(json.dumps({"metric": "detector ablation against the uniform baseline (Table 2 analogue)",
+                      "config": {**_config(w), "frames": F, "first_frame": k0, "tau2": 3}, "rows": rows}),
+          flush=True)
+
+
 # ------------------------------------------------------------------ our arm
 def main():
     args = parse()
@@ -420,6 +470,8 @@ def main():
         return run_batch(args)
     if args.workload == "quality":
         return run_quality(args)
+    if args.workload == "ablation":
+        return run_ablation(args)
     import numpy as np
     import torch
 
