@@ -255,9 +255,19 @@ def test_terrain_full_frame_sampled_pixels(terrain):
     """The benchmark's configuration at full size (1280x720, 8192-spp
     reference, 512/+64/8192 schedule, 32M-path wavefront), checked on
     sampled pixels the oracle recomputes one by one."""
-    w, osc = terrain
+    _full_frame_sampled(*terrain, 0)
+
+
+@pytest.mark.slow
+def test_spheres_full_frame_sampled_pixels(spheres):
+    """Config 2 at full size (512x512, 64 displaced icospheres, one spinning:
+    a moving instance under a per-frame TLAS), keyframes 4 -> 5."""
+    _full_frame_sampled(*spheres, 4)
+
+
+def _full_frame_sampled(w, osc, k):
     r = renderer_for(w)
-    out = r.render_events(w.times[0], w.times[1], w.C, w.alpha, w.spp_batch, w.spp_max)
+    out = r.render_events(w.times[k], w.times[k + 1], w.C, w.alpha, w.spp_batch, w.spp_max)
     ev = out["events"].cpu().numpy().reshape(-1)
     n = out["spp"].cpu().numpy().reshape(-1)
     mean = out["mean"].cpu().numpy().reshape(-1)
@@ -266,16 +276,16 @@ def test_terrain_full_frame_sampled_pixels(terrain):
     pix = np.unique(np.concatenate([rng.choice(w.width * w.height, size=112, replace=False),
                                     rng.choice(evpix, size=min(32, evpix.size), replace=False)])).astype(np.int32)
     p, det = O.params_of(w), O.detect_of(w)
-    ref = O.render_events(osc, p, det, w.times[0], w.times[1], pix)
-    s0 = per_sample(r, osc, p, w.times[0], pix, 0, w.spp_max, w.eps)
+    ref = O.render_events(osc, p, det, w.times[k], w.times[k + 1], pix)
+    s0 = per_sample(r, osc, p, w.times[k], pix, 0, w.spp_max, w.eps)
     k1 = int(max(n[pix].max(), ref["n"].max()))
-    s1 = per_sample(r, osc, p, w.times[1], pix, 0, k1, w.eps)
+    s1 = per_sample(r, osc, p, w.times[k + 1], pix, 0, k1, w.eps)
     used1 = np.arange(k1)[None, :] < np.maximum(n[pix], ref["n"])[:, None]
     m0 = s0["match"].all(1)
     m1 = np.where(used1, s1["match"], True).all(1)
     q = 1 - np.concatenate([s0["match"].reshape(-1), s1["match"][used1]]).mean()
     keep = m0 & m1 & (ref["margin_t"] >= T_BAND) & (ref["margin_c"] >= C_BAND)
-    print("terrain full frame: sample mismatch %.2e, kept %d of %d sampled pixels" % (q, keep.sum(), pix.size))
+    print("%s full frame: sample mismatch %.2e, kept %d of %d sampled pixels" % (w.name, q, keep.sum(), pix.size))
     assert q <= SAMPLE_MISMATCH
     # each sampled pixel draws ~(spp_max + n) samples; it is set aside when
     # any of them took a different discrete decision in FP32 and FP64
