@@ -106,7 +106,10 @@ typedef struct {
     int32_t variant;    /* MCEV_ONE_TAILED ... MCEV_UNIFORM */
     int32_t se_mode;    /* MCEV_SE_PAPER or MCEV_SE_WELCH */
     uint64_t seed;      /* Philox key seed */
-    int64_t wavefront;  /* max paths in flight per chunk; 0 = library default */
+    int64_t wavefront;  /* max paths in flight per chunk (1024..2^30); 0 = library default (2^25).
+                           A chunk holds all of a pixel's samples of one round, so calls
+                           whose per-pixel sample count (spp_max, count, spp) exceeds it
+                           fail with MCEV_ERR_ARG */
     int32_t profile;    /* 1: time every kernel launch with CUDA events (mcev_stats.kernel_ms) */
     int32_t batch_window; /* after the first batch, a round may trace up to this many batches of
                              spp_batch per undecided pixel at once (as many as fill the wavefront),

@@ -632,8 +632,21 @@ mcev_status frame_setup(mcev_ctx* ctx, double t, int slot) {
 }
 
 // ---------------------------------------------------------------- buffers
+int64_t wave_cap(const mcev_ctx* ctx) {
+    return ctx->params.wavefront > 0 ? ctx->params.wavefront : ((int64_t)1 << 25);
+}
+
+// Every chunk holds all the samples one call draws for a pixel in a round, so
+// a per-pixel sample count above the wavefront capacity is refused.
+mcev_status check_spp_fits(mcev_ctx* ctx, int64_t spp) {
+    if (spp > wave_cap(ctx))
+        return fail(ctx, MCEV_ERR_ARG, "%lld samples per pixel exceed the wavefront (%lld paths)", (long long)spp,
+                    (long long)wave_cap(ctx));
+    return MCEV_OK;
+}
+
 mcev_status ensure_wave(mcev_ctx* ctx) {
-    const int64_t cap = ctx->params.wavefront > 0 ? ctx->params.wavefront : ((int64_t)1 << 25);
+    const int64_t cap = wave_cap(ctx);
     if (ctx->d_wave.ptr && ctx->wave.cap == cap) return MCEV_OK;
     // path slots: L, sig, pflags, pix_k, Ltot, delta; per ray-queue slot (x2):
     // ray_o, ray_d, ray_s; hit; shadow: sh_o, sh_d, sh_c, sh_g, sh_m
@@ -1126,6 +1139,7 @@ mcev_status mcev_set_params(mcev_ctx* ctx, const mcev_params* p) {
 mcev_status mcev_render_reference(mcev_ctx* ctx, double t0, int32_t spp) {
     ST(check_ready(ctx));
     if (spp < 2) return fail(ctx, MCEV_ERR_ARG, "spp must be >= 2");
+    ST(check_spp_fits(ctx, spp));
     reset_call_counters(ctx);
     return do_reference(ctx, t0, spp, nullptr);
 }
@@ -1137,6 +1151,7 @@ mcev_status mcev_render_events(mcev_ctx* ctx, double t0, double t1, float C, flo
     if (!events_out) return fail(ctx, MCEV_ERR_ARG, "events_out is required");
     if (!(C >= 0.0f) || !(alpha > 0.0f && alpha < 1.0f) || spp_batch < 1 || spp_max < ctx->params.spp_min)
         return fail(ctx, MCEV_ERR_ARG, "need C >= 0, 0 < alpha < 1, spp_batch >= 1, spp_max >= spp_min");
+    ST(check_spp_fits(ctx, spp_max));
     reset_call_counters(ctx);
     CU(cudaMemsetAsync(ctx->wave.counters + 4, 0, 60 * sizeof(int32_t), ctx->stream));
     CU(cudaEventRecord(ctx->ev0, ctx->stream));
@@ -1176,6 +1191,7 @@ mcev_status mcev_trace_samples(mcev_ctx* ctx, double t, const int32_t* pixels, i
         return fail(ctx, MCEV_ERR_ARG, "bad trace_samples sizes");
     if (n_pix == 0) return MCEV_OK;
     if (!pixels || !L_out) return fail(ctx, MCEV_ERR_ARG, "null pixels or L_out");
+    ST(check_spp_fits(ctx, count));
     reset_call_counters(ctx);
     ST(frame_setup(ctx, t, 0));
     const DevParams P = dev_params(ctx, sig_out != nullptr);
@@ -1209,6 +1225,7 @@ mcev_status mcev_set_emission(mcev_ctx* ctx, const float* emission, int32_t n_ma
 mcev_status mcev_render_mean(mcev_ctx* ctx, double t, int32_t spp, float* mean_out) {
     ST(check_ready(ctx));
     if (spp < 1 || !mean_out) return fail(ctx, MCEV_ERR_ARG, "need spp >= 1 and mean_out");
+    ST(check_spp_fits(ctx, spp));
     reset_call_counters(ctx);
     ST(frame_setup(ctx, t, 0));
     StatsArgs A{};
@@ -1225,6 +1242,7 @@ mcev_status mcev_backward(mcev_ctx* ctx, double t, int32_t spp, const float* gra
                           float* grad_emission) {
     ST(check_ready(ctx));
     if (spp < 1 || !grad_mean) return fail(ctx, MCEV_ERR_ARG, "need spp >= 1 and grad_mean");
+    ST(check_spp_fits(ctx, spp));
     if (grad_texture && !ctx->dsc.tex) return fail(ctx, MCEV_ERR_STATE, "no texture set");
     reset_call_counters(ctx);
     ST(frame_setup(ctx, t, 0));
@@ -1262,6 +1280,7 @@ mcev_status mcev_render_events_batch(mcev_ctx* runner, const mcev_job* jobs, int
     if (!j0c) return fail(ctx, MCEV_ERR_ARG, "job 0 has no context");
     const int32_t spp_min = j0c->params.spp_min, variant = j0c->params.variant, se_mode = j0c->params.se_mode;
     if (spp_max < spp_min) return fail(ctx, MCEV_ERR_ARG, "spp_max < spp_min");
+    ST(check_spp_fits(ctx, spp_max));
     for (int i = 0; i < n_jobs; ++i) {
         const mcev_ctx* c = jobs[i].ctx;
         if (!c || !c->have_scene) return fail(ctx, MCEV_ERR_STATE, "job %d: no context or no scene", i);

@@ -196,6 +196,15 @@ def test_errors_are_statuses_not_crashes():
         r.render_events(0.0, 1.0, 0.2, 1.5, 16, 256)
     with pytest.raises(McevError, match="ARG"):
         r.set_params(spp_min=1)
+    # per-pixel sample counts above the wavefront capacity are refused before any launch
+    r.set_params(wavefront=1024)
+    with pytest.raises(McevError, match="exceed the wavefront"):
+        r.render_events(0.0, 1.0, 0.2, 0.05, 16, 2048)
+    with pytest.raises(McevError, match="exceed the wavefront"):
+        r.trace_samples(0.0, torch.arange(4, dtype=torch.int32), 0, 1025)
+    with pytest.raises(McevError, match="exceed the wavefront"):
+        r.render_reference(0.0, 4096)
+    r.set_params(wavefront=0)
     bad = sg.cornell_box()
     bad.triangles = bad.triangles.copy()
     bad.triangles[0, 0] = 10 ** 6
