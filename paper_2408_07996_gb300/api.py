@@ -201,24 +201,34 @@ class Renderer:
             L.check(self.lib.mcev_set_texture(self.ctx, None, 0, 0), self.ctx, "mcev_set_texture")
             self._texture = None
             return
-        assert texture.is_cuda and texture.dtype == torch.float32 and texture.is_contiguous()
+        if not (texture.is_cuda and texture.dtype == torch.float32 and texture.is_contiguous() and
+                texture.dim() == 3 and texture.shape[2] == 3):
+            raise ValueError("texture must be a contiguous float32 CUDA tensor [H, W, 3]")
         self._texture = texture
         L.check(self.lib.mcev_set_texture(self.ctx, _tptr(texture), texture.shape[1], texture.shape[0]), self.ctx,
                 "mcev_set_texture")
 
     def set_emission(self, emission: torch.Tensor | None) -> None:
-        """Emitted radiance per material on the device (kept by reference)."""
+        """Emitted radiance per material on the device (kept by reference);
+        it replaces the table's value for the scene's emissive materials."""
+        if emission is not None and not (emission.is_cuda and emission.dtype == torch.float32 and
+                                         emission.is_contiguous()):
+            raise ValueError("emission must be a contiguous float32 CUDA tensor")
         self._emission = emission
         n = 0 if emission is None else emission.numel()
         L.check(self.lib.mcev_set_emission(self.ctx, _tptr(emission), n), self.ctx, "mcev_set_emission")
 
     def render_mean(self, t: float, spp: int) -> torch.Tensor:
+        """Per-pixel mean of ln(L + eps) over samples 0..spp-1 at time t."""
         out = torch.empty((self.height, self.width), dtype=torch.float32, device=self.device)
         L.check(self.lib.mcev_render_mean(self.ctx, float(t), int(spp), _tptr(out)), self.ctx, "mcev_render_mean")
         return out
 
     def backward(self, t: float, spp: int, grad_mean: torch.Tensor, grad_texture: torch.Tensor | None,
                  grad_emission: torch.Tensor | None) -> None:
+        """Path-replay adjoint of render_mean(t, spp): adds d loss / d texel RGB
+        to grad_texture and d loss / d emitted radiance to grad_emission, given
+        grad_mean = d loss / d mean [H, W]."""
         g = grad_mean.to(device=self.device, dtype=torch.float32).contiguous()
         L.check(self.lib.mcev_backward(self.ctx, float(t), int(spp), _tptr(g), _tptr(grad_texture),
                                        _tptr(grad_emission)), self.ctx, "mcev_backward")
@@ -274,7 +284,9 @@ def event_quality(a: torch.Tensor, b: torch.Tensor, tau2: int = 3, want_d2: bool
     computed by mcev_event_quality.  `runner`: a context to run on (its
     stream and allocator); by default one cached per device.  With
     `want_d2`, also the per-voxel squared distances d2_a, d2_b."""
-    assert a.shape == b.shape and a.dtype == torch.int8 and b.dtype == torch.int8 and a.is_cuda and b.is_cuda
+    if not (a.shape == b.shape and a.dim() in (2, 3) and a.dtype == torch.int8 and b.dtype == torch.int8 and
+            a.is_cuda and b.is_cuda):
+        raise ValueError("a and b must be int8 CUDA tensors of one shape, [T, H, W] or [H, W]")
     shp = (1,) * (3 - a.dim()) + tuple(a.shape)
     T, H, W = shp
     if runner is None:
