@@ -348,6 +348,19 @@ def test_small_frame_edge_cases(cornell, case):
     r.close()
 
 
+@pytest.mark.parametrize("W,H", [(1, 1), (37, 1), (1, 29)])
+def test_degenerate_image_sizes(cornell, W, H):
+    w0, osc = cornell
+    w = sg.workload("cornell64")
+    r = renderer_for(w, width=W, height=H)
+    res = _event_parity(r, osc, w, O.detect_of(w), 0.0, 1.0, H, W, O.params_of(w, width=W, height=H))
+    assert res["bad_ev"].sum() == 0 and res["bad_n"].sum() == 0
+    if res["dmean"].size:
+        assert res["dmean"].max() < MEAN_TOL
+    assert res["out"]["events"].shape == (H, W)
+    r.close()
+
+
 def test_trace_samples_empty_and_ragged(cornell):
     w, osc = cornell
     r = renderer_for(w, wavefront=1024)
