@@ -93,6 +93,7 @@ struct mcev_ctx {
 
     // device scene
     DevBuf d_quality;                       // event-quality scratch: two int32 volumes + accumulators
+    DevBuf d_gemit;                         // FP64 emission-gradient accumulator of mcev_backward
     DevBuf d_nodes, d_tris, d_uv, d_mats, d_env, d_marg, d_cond, d_tpdf;
     DevScene dsc{};
     Frame frames[2];
@@ -959,7 +960,7 @@ void mcev_destroy(mcev_ctx* ctx) {
     cudaStreamSynchronize(ctx->stream);
     DevBuf* bufs[] = {&ctx->d_nodes, &ctx->d_tris, &ctx->d_uv, &ctx->d_mats, &ctx->d_env, &ctx->d_marg, &ctx->d_cond,
                       &ctx->d_tpdf, &ctx->frames[0].buf, &ctx->frames[1].buf, &ctx->d_wave, &ctx->d_counters,
-                      &ctx->d_pix, &ctx->d_tcrit, &ctx->d_jobs, &ctx->d_bqueue, &ctx->d_quality};
+                      &ctx->d_pix, &ctx->d_tcrit, &ctx->d_jobs, &ctx->d_bqueue, &ctx->d_quality, &ctx->d_gemit};
     for (DevBuf* b : bufs) dev_free(ctx, *b);
     for (cudaEvent_t e : ctx->evpool) cudaEventDestroy(e);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
@@ -1254,7 +1255,11 @@ mcev_status mcev_backward(mcev_ctx* ctx, double t, int32_t spp, const float* gra
     Padj.spp = spp;
     Padj.grad_mean = grad_mean;
     Padj.grad_tex = grad_texture;
-    Padj.grad_emit = grad_emission;
+    if (grad_emission) {
+        ST(dev_alloc(ctx, ctx->d_gemit, sizeof(double) * std::max(1, ctx->n_mats)));
+        CU(cudaMemsetAsync(ctx->d_gemit.ptr, 0, sizeof(double) * std::max(1, ctx->n_mats), ctx->stream));
+        Padj.grad_emit = (double*)ctx->d_gemit.ptr;
+    }
     const int64_t per_chunk = std::max<int64_t>(1, ctx->wave.cap / spp);
     for (int64_t j0 = 0; j0 < npix; j0 += per_chunk) {
         const int64_t nj = std::min(per_chunk, npix - j0);
@@ -1264,6 +1269,8 @@ mcev_status mcev_backward(mcev_ctx* ctx, double t, int32_t spp, const float* gra
                            ctx->stream));
         ST(trace_chunk(ctx, ctx->frames[0], Padj, ctx->queue[0], j0, spp, 0, nj * spp, nullptr));
     }
+    if (grad_emission && ctx->n_mats > 0)
+        LAUNCH(MCEV_K_STATS, launch_add_f64(grad_emission, (const double*)ctx->d_gemit.ptr, ctx->n_mats, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
     ST(drain_events(ctx));
     return MCEV_OK;

@@ -237,7 +237,7 @@ __global__ void MCEV_SHADE_BOUNDS k_shade(DevScene sc, DevFrame fr, DevParams P,
                     }
                 }
                 L += beta * wgt * emit;
-                if (Q.adjoint && Q.grad_emit) atomicAdd(Q.grad_emit + mat, dlt * beta * wgt);
+                if (Q.adjoint && Q.grad_emit) atomicAdd(Q.grad_emit + mat, (double)(dlt * beta * wgt));
             }
             if (depth < Q.max_depth && alb > 0.0f) {
                 // adjoint: every contribution after this vertex carries one factor of its albedo
@@ -359,7 +359,8 @@ __global__ void MCEV_TRAV_BOUNDS k_shadow(DevScene sc, DevFrame fr, DevParams P,
         if (!occluded(S, F, xyz(o), xyz(d), Q.t_min, d.w, &e, work)) {
             w.L[p] += w.sh_c[i];
             if (Q.want_sig) w.pflags[p] |= 4u;
-            if (Q.adjoint && Q.grad_emit && w.sh_m[i] >= 0) atomicAdd(Q.grad_emit + w.sh_m[i], w.delta[p] * w.sh_g[i]);
+            if (Q.adjoint && Q.grad_emit && w.sh_m[i] >= 0)
+                atomicAdd(Q.grad_emit + w.sh_m[i], (double)(w.delta[p] * w.sh_g[i]));
         }
     }
     if (e) atomicOr(err, 1);
@@ -621,6 +622,17 @@ static cudaError_t launch_stats_checked(const Wave& w, const StatsArgs& A, const
                                         int32_t* next_queue, int sms, cudaStream_t st) {
     k_stats<true, false><<<grid_for(n_pix * 32, 256, sms, 8), 256, 0, st>>>(w, A, queue, 0, n_pix, next_queue,
                                                                              nullptr);
+    return cudaGetLastError();
+}
+
+// out[i] += (float)acc[i]
+__global__ void k_add_f64(float* __restrict__ out, const double* __restrict__ acc, int n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        out[i] += (float)acc[i];
+}
+
+cudaError_t launch_add_f64(float* out, const double* acc, int n, cudaStream_t st) {
+    k_add_f64<<<(n + 255) / 256, 256, 0, st>>>(out, acc, n);
     return cudaGetLastError();
 }
 

@@ -39,6 +39,8 @@ cudaError_t launch_shadow(const DevScene& sc, const DevFrame& fr, const DevParam
                           int32_t* err, int sms, cudaStream_t st, const Job* jobs);
 cudaError_t launch_stats(const Wave& w, const StatsArgs& A, const int32_t* queue, int64_t j0, int64_t n_pix,
                          int32_t* next_queue, int sms, cudaStream_t st, const Job* jobs);
+// out[i] += (float)acc[i] for i < n (the adjoint's FP64 emission accumulator)
+cudaError_t launch_add_f64(float* out, const double* acc, int n, cudaStream_t st);
 cudaError_t launch_fill_entries(int32_t* q, int64_t n, int job, int sms, cudaStream_t st);
 cudaError_t launch_write_samples(const Wave& w, int64_t out0, int64_t n_paths, float* L_out, uint32_t* sig_out,
                                  int sms, cudaStream_t st);

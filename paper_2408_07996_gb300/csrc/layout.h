@@ -90,7 +90,8 @@ struct DevParams {
     int32_t spp;              // samples per pixel of the replayed frame
     const float* grad_mean;   // d loss / d mean ln(L + eps), per pixel
     float* grad_tex;          // accumulated d loss / d texel RGB
-    float* grad_emit;         // accumulated d loss / d emitted radiance, per material
+    double* grad_emit;        // accumulated d loss / d emitted radiance, per material (FP64:
+                              // millions of contributions land on a few materials)
 };
 
 // Wavefront buffers of one chunk (capacity = `cap` paths).
