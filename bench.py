@@ -252,13 +252,14 @@ def run_batch(args):
 
     for k in range(Wm):
         frame(k)
-    # autotune on the next frame pair of the first 16 jobs (their references
-    # exist, so a trial costs one adaptive frame); states are restored
+    # autotune on the next frame pair of all jobs (their references exist,
+    # so a trial costs one batched adaptive frame; the wavefront that suits a
+    # subset of the jobs does not suit all of them); states are restored
     tune = None
     if not args.no_tune:
-        tune = tune_batch(runner, rs[:16], (times[Wm], times[Wm + 1]), sched,
-                          wavefronts=(1 << 23, 1 << 25), windows=(4, 16), leaf_sizes=(2, 4))
-        tune = {"best": tune["best"], "trials": len(tune["trials"]), "jobs": 16}
+        tune = tune_batch(runner, rs, (times[Wm], times[Wm + 1]), sched,
+                          wavefronts=(1 << 24, 1 << 25), windows=(16,), leaf_sizes=(2, 4))
+        tune = {"best": tune["best"], "trials": len(tune["trials"]), "jobs": len(rs)}
     torch.cuda.synchronize()
     clocks = Clocks(0)
     clocks.start()

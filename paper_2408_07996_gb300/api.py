@@ -6,7 +6,7 @@ in the library's kernels."""
 from __future__ import annotations
 
 import ctypes as C
-from dataclasses import dataclass
+from dataclasses import dataclass, replace
 
 import numpy as np
 import torch
@@ -147,15 +147,16 @@ class Renderer:
         L.check(self.lib.mcev_build_bvh(self.ctx, sah_bins, max_leaf), self.ctx, "mcev_build_bvh")
 
     def set_params(self, **kw) -> RenderSettings:
-        for k, v in kw.items():
+        """Updates the named settings; on an error the previous settings stay."""
+        for k in kw:
             if not hasattr(self.settings, k):
                 raise KeyError(k)
-            setattr(self.settings, k, v)
-        s = self.settings
+        s = replace(self.settings, **kw)
         p = L.Params(eps=s.eps, t_min=s.t_min, max_depth=s.max_depth, nee=s.nee, mis=s.mis,
                      spp_min=s.spp_min, variant=s.variant, se_mode=s.se_mode, seed=s.seed,
                      wavefront=s.wavefront, profile=s.profile, batch_window=s.batch_window)
         L.check(self.lib.mcev_set_params(self.ctx, C.byref(p)), self.ctx, "mcev_set_params")
+        self.settings = s
         return s
 
     def configure(self, w) -> None:
