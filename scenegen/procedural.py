@@ -562,7 +562,7 @@ def albedo_texture(size: int = 512, seed: int = 0, lo: float = 0.2, hi: float = 
 
 def textured_room(seed: int = 20240819, grid: int = 158, tex_size: int = 512, shift: float = 0.05,
                   texture: np.ndarray | None = None) -> Scene:
-    """Differentiation scene (config 5): a (grid-1)^2*2-triangle floor (about
+    """Differentiation scene (256x256 frames, 64 spp): a (grid-1)^2*2-triangle floor (about
     50k triangles at grid 158) carrying an RGB albedo texture, a few
     untextured boxes, and 4 one-sided emissive quads (one material each)
     above it.  Camera looks down at the floor and shifts by `shift` along x
@@ -618,7 +618,7 @@ BATCH_RESOLUTIONS = ((128, 128), (320, 240), (346, 260), (640, 480))
 
 
 def batch_workloads(n_jobs: int = 64, seed: int = 20240818) -> list:
-    """Independent frame-pair jobs for batched rendering (config 4): image
+    """Independent frame-pair jobs for batched rendering: image
     sizes drawn uniformly from BATCH_RESOLUTIONS, scenes of 5k-100k
     triangles (displaced icosphere fields of 1-19 level-4 spheres, or 4-78
     level-3 spheres, each with one spinning sphere and a moving camera),

@@ -14,7 +14,7 @@ from parity import per_sample, renderer_for, summary
 
 pytestmark = pytest.mark.gpu
 
-MEAN_TOL = 1e-4      # per-pixel mean ln L, absolute (spec tolerance)
+MEAN_TOL = 1e-4      # per-pixel mean ln L, absolute
 T_BAND = 1e-3        # |t - t_crit| band where FP32/FP64 decisions may differ
 C_BAND = 1e-5        # | |gap| - C | band
 SAMPLE_MISMATCH = 2e-3   # max fraction of samples with different discrete decisions
@@ -269,7 +269,7 @@ def test_terrain_full_frame_sampled_pixels(terrain):
 
 @pytest.mark.slow
 def test_spheres_full_frame_sampled_pixels(spheres):
-    """Config 2 at full size (512x512, 64 displaced icospheres, one spinning:
+    """The 512x512 sphere field at full size (64 displaced icospheres, one spinning:
     a moving instance under a per-frame TLAS), keyframes 4 -> 5."""
     _full_frame_sampled(*spheres, 4)
 
