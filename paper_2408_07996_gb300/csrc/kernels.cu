@@ -5,9 +5,10 @@
 // where extend/shade/shadow consume device-side ray queues (sizes in device
 // counters, no host round trip) and `stats` fuses, per queued pixel, the
 // log-luminance batch statistics (Sec. 3.1, Eq. 3-4), the Chan merge into the
-// running statistics, the t-test of Eq. 7 (Sec. 3.2), the warp-aggregated
-// re-queue of undecided pixels (Sec. 3.3) and the event rule with the
-// reference update (Alg. 1, Eq. 1).
+// running statistics, the t-test of Eq. 7 (Sec. 3.2), the re-queue of
+// undecided pixels (Sec. 3.3; one atomic per warp, since a warp owns a pixel)
+// and the event rule with the reference update (Alg. 1, Eq. 1).  Rays and
+// shadow rays are appended to their queues with warp-aggregated atomics.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
