@@ -196,11 +196,14 @@ mcev_status mcev_render_reference(mcev_ctx* ctx, double t0, int32_t spp);
  *   events_out : device int8 [H*W], required: -1, 0, +1 per pixel
  *   spp_out    : device int32 [H*W] or NULL: samples used per pixel
  *   mean_out   : device float [H*W] or NULL: mean ln(L + eps) at t1
- *   stats_out  : host or NULL; when non-NULL the call synchronises and fills it
+ *   stats_out  : host or NULL; filled when non-NULL
+ * The call returns when the frame is done: each round reads the number of
+ * undecided pixels back to the host to size the next round, so the stream is
+ * synchronised several times per call.
  * Sample k of pixel p at time t uses the same random numbers in every mode,
  * so adaptive samples are a prefix of the uniform ones.
- * Errors: ARG (C < 0, alpha outside (0,1), spp_batch < 1, spp_max < spp_min),
- * STATE, OOM, CUDA. */
+ * Errors: ARG (C < 0, alpha outside (0,1), spp_batch < 1, spp_max < spp_min,
+ * spp_max above the wavefront), STATE, OOM, CUDA. */
 mcev_status mcev_render_events(mcev_ctx* ctx, double t0, double t1, float C, float alpha,
                                int32_t spp_batch, int32_t spp_max, int8_t* events_out,
                                int32_t* spp_out, float* mean_out, mcev_stats* stats_out);
