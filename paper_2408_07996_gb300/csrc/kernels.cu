@@ -441,10 +441,19 @@ __global__ void __launch_bounds__(256) k_stats(Wave w, StatsArgs A0, const int32
         const float* Lp = w.L + j * A.spp_r;
         for (int s0 = 0; s0 < A.spp_r && !decided; s0 += A.sub) {
             const int s1 = min(s0 + A.sub, A.spp_r);
-            // per-lane moments of the lane's samples of this batch, from sums
-            // shifted by the lane's first sample (no division per sample)
-            Moments m{0.0f, 0.0f, 0.0f};
-            float y0 = 0.0f, s1d = 0.0f, s2d = 0.0f;
+            // moments of this batch from sums shifted by one warp-uniform value
+            // (the running mean, or the batch's first sample for a pixel's
+            // first batch), so lanes merge by plain addition: the butterfly
+            // below adds a + b on one lane and b + a on its partner, which
+            // are the same bits, so every lane ends with identical sums
+            float sh;
+            if (c.n > 0.0f) {
+                sh = c.mean;
+            } else {
+                const float L0 = Lp[s0];
+                sh = MCEV_LOG((isfinite(L0) ? L0 : 0.0f) + A.eps);
+            }
+            float s1d = 0.0f, s2d = 0.0f;
             int cnt = 0;
             for (int s = s0 + lane; s < s1; s += 32) {
                 float Lv = Lp[s];
@@ -452,26 +461,22 @@ __global__ void __launch_bounds__(256) k_stats(Wave w, StatsArgs A0, const int32
                     Lv = 0.0f;
                     ++bad;
                 }
-                const float y = MCEV_LOG(Lv + A.eps);
-                if (cnt == 0) y0 = y;
-                const float d = y - y0;
+                const float d = MCEV_LOG(Lv + A.eps) - sh;
                 s1d += d;
                 s2d = fmaf(d, d, s2d);
                 ++cnt;
             }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                s1d += __shfl_xor_sync(0xffffffffu, s1d, off);
+                s2d += __shfl_xor_sync(0xffffffffu, s2d, off);
+                cnt += __shfl_xor_sync(0xffffffffu, cnt, off);
+            }
+            Moments m{0.0f, 0.0f, 0.0f};
             if (cnt > 0) {
                 const float fn = (float)cnt;
                 const float md = s1d / fn;
-                m = Moments{fn, y0 + md, fmaxf(s2d - s1d * md, 0.0f)};
-            }
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) {
-                Moments o;
-                o.n = __shfl_xor_sync(0xffffffffu, m.n, off);
-                o.mean = __shfl_xor_sync(0xffffffffu, m.mean, off);
-                o.m2 = __shfl_xor_sync(0xffffffffu, m.m2, off);
-                // merge in a fixed lane order so every lane gets identical bits
-                m = (lane & off) ? chan(o, m) : chan(m, o);
+                m = Moments{fn, sh + md, fmaxf(s2d - s1d * md, 0.0f)};
             }
             c = (A.k_base == 0 && s0 == 0) ? m : chan(c, m);
             n = (int32_t)c.n;
