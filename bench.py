@@ -41,6 +41,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="terrain720p")
     ap.add_argument("--frames", type=int, default=5, help="video length of --workload ablation")
+    ap.add_argument("--scene", default="terrain720p", help="workload that --workload ablation renders")
     ap.add_argument("--dims", type=int, nargs=3, default=None, metavar=("W", "H", "T"),
                     help="video size of --workload quality (default 1280 720 100)")
     ap.add_argument("--no-uniform", action="store_true")
@@ -412,8 +413,8 @@ def traversal_l1_peak(local: int) -> dict:
 
 
 def run_ablation(args):
-    """The paper's comparison (Sec. 4.2, Table 2) on the terrain workload: a
-    short event video (frames t_3 -> t_{3+F}) rendered from the same
+    """The paper's comparison (Sec. 4.2, Table 2) on one workload (--scene,
+    default the terrain): a short event video (frames t_3 -> t_{3+F}) rendered from the same
     reference by the uniform-spp baseline and by each detector variant
     (one-tailed t-test = the paper's method, mean-only and two-tailed
     ablations, Welch standard error), each scored against the uniform video
@@ -424,7 +425,7 @@ def run_ablation(args):
     from paper_2408_07996_gb300 import MEAN_ONLY, ONE_TAILED, SE_WELCH, TWO_TAILED, UNIFORM
     from paper_2408_07996_gb300.api import Renderer, event_quality
 
-    w = sg.workload(args.workload if args.workload != "ablation" else "terrain720p")
+    w = sg.workload(args.scene)
     F = args.frames
     k0 = 3
     r = Renderer(w.width, w.height, 0)

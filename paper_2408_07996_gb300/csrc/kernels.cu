@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(256) k_raygen(DevFrame fr, DevParams P, Wave w
         w.ray_o[cur][p] = make_float4(F.eye[0], F.eye[1], F.eye[2], __int_as_float((int)p));
         w.ray_d[cur][p] = make_float4(d.x, d.y, d.z, __int_as_float(job << 8));
         w.L[p] = 0.0f;
-        w.pix_k[p] = make_int2(entry, (int)k);
+        if (kBatch) w.pix_k[p] = make_int2(entry, (int)k);   // the shadow kernel's job lookup
         w.ray_s[cur][p] = make_float4(1.0f, 0.0f, __int_as_float(entry), __int_as_float((int)k));
         if (Q.adjoint && Q.grad_mean) {
             // d loss / d L of this path: d loss / d mean * d mean / d ln(L + eps) * d ln(L + eps) / dL

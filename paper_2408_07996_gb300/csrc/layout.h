@@ -100,7 +100,7 @@ struct Wave {
     float* L;
     uint32_t* sig;
     uint32_t* pflags;         // pending flags of the last vertex (0xFFFFFFFF = none)
-    int2* pix_k;              // (pixel, sample index)
+    int2* pix_k;              // (queue entry, sample index); written for batched renders only
     // ray queues (ping-pong) and hits, per queue slot
     float4* ray_o[2];         // xyz origin, w = path slot (int bits)
     float4* ray_d[2];         // xyz direction, w = depth (int bits)
