@@ -357,6 +357,9 @@ mcev_status build_blas(mcev_ctx* ctx) {
     size_t n_static_tris = 0;
     for (int i = 0; i < ni; ++i)
         if (ctx->inst_static[i]) n_static_tris += (size_t)ctx->meshes[ctx->inst_mesh[i]].n_tri;
+    // kernels address triangles as 3 * index in 32-bit arithmetic
+    if (tris.size() / 3 + n_static_tris > ((size_t)1 << 29))
+        return fail(ctx, MCEV_ERR_ARG, "more than 2^29 triangles once never-moving instances are baked");
     ctx->static_vtx.resize(9 * n_static_tris);
     ssrc.reserve(n_static_tris);
     size_t w = 0;
