@@ -284,7 +284,7 @@ def run_batch(args):
             "mpaths_per_s": paths / (ms / 1e3) / 1e6, "rounds_per_step": sum(s["rounds"] for s in steps) / K,
             "gpu_launches": sum(s["kernel_launches"] for s in steps),
             "kernel_share": {n: round(kms[i] / total, 4) if total else None
-                             for i, n in enumerate(["raygen", "extend", "shade", "shadow", "stats"])},
+                             for i, n in enumerate(["raygen", "traversal", "shade", "shadow", "stats"])},
             "launch_gaps_ms_per_step": (sum(s["gpu_ms"] for s in steps) - total) / K,
             "autotune": tune, "clocks": clk}
     # the same frame rendered job after job (one-job batches through the same
@@ -606,30 +606,33 @@ def main():
     mpaths = job_rate(paths, ms / 1e3, world) / 1e6
     launches = sum(s["kernel_launches"] for s in steps)
 
-    # roofline of the dominant kernel (closest-hit traversal), from the
-    # timed steps: per-launch device time (CUDA events on the library's
-    # stream) and the traversal work the kernel did
+    # roofline of the dominant work, BVH traversal (closest-hit and shadow
+    # rays; a bounce's shadow rays share a launch with the next bounce's
+    # closest hits), from the timed steps: device time of the traversal
+    # launches (CUDA events on the library's stream) and the traversal work
+    # they did
     kms = [sum(s["kernel_ms"][i] for s in steps) for i in range(5)]
     kcnt = [sum(s["kernel_count"][i] for s in steps) for i in range(5)]
-    nodes = sum(s["nodes_closest"] for s in steps)
-    tris = sum(s["tris_closest"] for s in steps)
-    ext_ms = kms[1]
+    nodes = sum(s["nodes_closest"] + s["nodes_shadow"] for s in steps)
+    tris = sum(s["tris_closest"] + s["tris_shadow"] for s in steps)
+    rays = sum(s["rays_closest"] + s["rays_shadow"] for s in steps)
+    ext_ms = kms[1] + kms[3]
     ops = nodes * OPS_PER_NODE + tris * OPS_PER_TRI
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     sm_max_mhz = clk.get("sm_max_mhz") or 2070.0
     peak_tops = sm_count * FP32_LANES_PER_SM * sm_max_mhz * 1e6 / 1e12
     achieved_tops = ops / (ext_ms / 1e3) / 1e12 if ext_ms > 0 else None
     total_kms = sum(kms)
-    roofline = {"kernel": "k_extend (closest-hit BVH traversal)", "bound": "alu",
+    roofline = {"kernel": "BVH traversal: k_extend, k_shadow_extend (closest-hit + shadow rays)", "bound": "alu",
                 "achieved": achieved_tops, "peak": peak_tops, "unit": "Tops/s (FP32 lane ops)",
                 "frac": (achieved_tops / peak_tops) if achieved_tops else None, "traffic": None,
-                "avg_launch_ms": ext_ms / max(1, kcnt[1]),
-                "ops_per_launch": ops / max(1, kcnt[1]),
-                "nodes_per_ray": nodes / max(1, sum(s["rays_closest"] for s in steps)),
-                "tris_per_ray": tris / max(1, sum(s["rays_closest"] for s in steps)),
-                "grays_per_s": sum(s["rays_closest"] for s in steps) / (ext_ms / 1e3) / 1e9 if ext_ms else None,
+                "avg_launch_ms": ext_ms / max(1, kcnt[1] + kcnt[3]),
+                "ops_per_launch": ops / max(1, kcnt[1] + kcnt[3]),
+                "nodes_per_ray": nodes / max(1, rays),
+                "tris_per_ray": tris / max(1, rays),
+                "grays_per_s": rays / (ext_ms / 1e3) / 1e9 if ext_ms else None,
                 "kernel_share": {n: round(kms[i] / total_kms, 4) if total_kms else None
-                                 for i, n in enumerate(["raygen", "extend", "shade", "shadow", "stats"])},
+                                 for i, n in enumerate(["raygen", "traversal", "shade", "shadow", "stats"])},
                 "peak_basis": f"{sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_max_mhz:.0f} MHz"}
 
     # statistics kernel against HBM

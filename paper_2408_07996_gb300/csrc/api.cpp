@@ -746,6 +746,11 @@ DevParams dev_params(const mcev_ctx* ctx, bool want_sig) {
         ST(ev_mark(ctx, cls, false));                                                                 \
     } while (0)
 
+// 1: a bounce's shadow rays share one launch with the next bounce's closest hits
+#ifndef MCEV_FUSE_SHADOW
+#define MCEV_FUSE_SHADOW 1
+#endif
+
 // one chunk of n_paths = nj * spp_r paths through every bounce
 // Batched render (several contexts' frame pairs in one set of rounds): the
 // device job table, the union queues of (job << 24 | pixel) entries, and the
@@ -769,11 +774,26 @@ mcev_status trace_chunk(mcev_ctx* ctx, const Frame& fr, const DevParams& P, cons
     const bool nee = B ? B->any_nee : P.nee != 0;
     LAUNCH(MCEV_K_RAYGEN, launch_raygen(fr.dev, P, w, queue, j0, spp_r, k_base, n_paths, 0, ctx->sms, ctx->stream, jobs));
     int cur = 0;
+    LAUNCH(MCEV_K_EXTEND, launch_extend(ctx->dsc, fr.dev, P.t_min, w, cur, n_paths, err, ctx->sms, ctx->stream, jobs));
     for (int depth = 0; depth <= depth_max; ++depth) {
-        LAUNCH(MCEV_K_EXTEND, launch_extend(ctx->dsc, fr.dev, P.t_min, w, cur, n_paths, err, ctx->sms, ctx->stream, jobs));
         LAUNCH(MCEV_K_SHADE, launch_shade(ctx->dsc, fr.dev, P, w, cur, n_paths, ctx->sms, ctx->stream, jobs));
-        if (depth < depth_max && nee)
-            LAUNCH(MCEV_K_SHADOW, launch_shadow(ctx->dsc, fr.dev, P, w, n_paths, err, ctx->sms, ctx->stream, jobs));
+        if (depth < depth_max) {
+#if MCEV_FUSE_SHADOW
+            // this bounce's shadow rays and the next bounce's closest hits in one launch
+            if (nee)
+                LAUNCH(MCEV_K_EXTEND, launch_shadow_extend(ctx->dsc, fr.dev, P, w, cur, n_paths, err, ctx->sms,
+                                                           ctx->stream, jobs));
+            else
+                LAUNCH(MCEV_K_EXTEND, launch_extend(ctx->dsc, fr.dev, P.t_min, w, cur ^ 1, n_paths, err, ctx->sms,
+                                                    ctx->stream, jobs));
+#else
+            if (nee)
+                LAUNCH(MCEV_K_SHADOW, launch_shadow(ctx->dsc, fr.dev, P, w, cur, n_paths, err, ctx->sms, ctx->stream,
+                                                    jobs));
+            LAUNCH(MCEV_K_EXTEND, launch_extend(ctx->dsc, fr.dev, P.t_min, w, cur ^ 1, n_paths, err, ctx->sms,
+                                                ctx->stream, jobs));
+#endif
+        }
         cur ^= 1;
     }
     return MCEV_OK;

@@ -36,6 +36,11 @@ namespace mcev {
 #endif
 
 static constexpr uint32_t NO_FLAGS = 0xFFFFFFFFu;
+
+// shadow-ray count of the bounce whose ray queue is `cur` (double-buffered so
+// a launch can trace one bounce's shadow rays while the next bounce's shade
+// appends to the other slot)
+__device__ __forceinline__ int sh_slot(int cur) { return cur ? 19 : 2; }
 static constexpr uint32_t FNV_BASIS = 2166136261u;
 
 // ------------------------------------------------------------------ raygen
@@ -50,7 +55,7 @@ __global__ void __launch_bounds__(256) k_raygen(DevFrame fr, DevParams P, Wave w
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         w.counters[cur] = (int32_t)n_paths;
         w.counters[1 - cur] = 0;
-        w.counters[2] = 0;
+        w.counters[2] = w.counters[19] = 0;
     }
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n_paths; p += (int64_t)gridDim.x * blockDim.x) {
         const int64_t j = p / spp_r;
@@ -99,18 +104,22 @@ __device__ __forceinline__ void add_work(const Wave& w, int which, int2 work) {
 }
 
 // ------------------------------------------------------------------ extend
+// Closest hits of the rays of queue `cur`, indices first, first + stride, ...
+// The first thread also clears the queue and shadow counters shade(cur) will
+// append to.
 template <bool kBatch>
-__global__ void MCEV_TRAV_BOUNDS k_extend(DevScene sc, DevFrame fr, float t_min, Wave w, int cur, int32_t* err,
-                                          const Job* __restrict__ jobs) {
+__device__ __forceinline__ void extend_rays(const DevScene& sc, const DevFrame& fr, float t_min, const Wave& w,
+                                            int cur, int32_t* err, const Job* __restrict__ jobs, int64_t first,
+                                            int64_t stride) {
     const int32_t n = *(volatile int32_t*)(w.counters + cur);
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (first == 0) {
         w.counters[1 - cur] = 0;
-        w.counters[2] = 0;
+        w.counters[sh_slot(cur)] = 0;
         atomicAdd(reinterpret_cast<unsigned long long*>(w.counters + 32) + 4, (unsigned long long)n);
     }
     int e = 0;
     int2 work = make_int2(0, 0);
-    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    for (int64_t i = first; i < n; i += stride) {
         const float4 o = w.ray_o[cur][i];
         const float4 d = w.ray_d[cur][i];
         const int job = kBatch ? (__float_as_int(d.w) >> 8) : 0;
@@ -122,6 +131,13 @@ __global__ void MCEV_TRAV_BOUNDS k_extend(DevScene sc, DevFrame fr, float t_min,
     }
     if (e) atomicOr(err, 1);
     add_work(w, WORK_CLOSEST, work);
+}
+
+template <bool kBatch>
+__global__ void MCEV_TRAV_BOUNDS k_extend(DevScene sc, DevFrame fr, float t_min, Wave w, int cur, int32_t* err,
+                                          const Job* __restrict__ jobs) {
+    extend_rays<kBatch>(sc, fr, t_min, w, cur, err, jobs, blockIdx.x * (int64_t)blockDim.x + threadIdx.x,
+                        (int64_t)gridDim.x * blockDim.x);
 }
 
 // ------------------------------------------------------------------ shade + NEE + BSDF sampling
@@ -321,7 +337,7 @@ __global__ void MCEV_SHADE_BOUNDS k_shade(DevScene sc, DevFrame fr, DevParams P,
             w.sig[p] = sig;
             w.pflags[p] = pflags;
         }
-        const int si = warp_append(w.counters + 2, shadow);
+        const int si = warp_append(w.counters + sh_slot(cur), shadow);
         if (shadow) {
             w.sh_o[si] = make_float4(P0.x, P0.y, P0.z, __int_as_float(p));
             w.sh_d[si] = make_float4(sh_dir.x, sh_dir.y, sh_dir.z, sh_tmax);
@@ -341,15 +357,16 @@ __global__ void MCEV_SHADE_BOUNDS k_shade(DevScene sc, DevFrame fr, DevParams P,
 }
 
 // ------------------------------------------------------------------ shadow rays
+// Shadow rays appended by shade(cur), indices first, first + stride, ...
 template <bool kBatch>
-__global__ void MCEV_TRAV_BOUNDS k_shadow(DevScene sc, DevFrame fr, DevParams P, Wave w, int32_t* err,
-                                          const Job* __restrict__ jobs) {
-    const int32_t n = *(volatile int32_t*)(w.counters + 2);
-    if (blockIdx.x == 0 && threadIdx.x == 0)
-        atomicAdd(reinterpret_cast<unsigned long long*>(w.counters + 32) + 5, (unsigned long long)n);
+__device__ __forceinline__ void shadow_rays(const DevScene& sc, const DevFrame& fr, const DevParams& P,
+                                            const Wave& w, int cur, int32_t* err, const Job* __restrict__ jobs,
+                                            int64_t first, int64_t stride) {
+    const int32_t n = *(volatile int32_t*)(w.counters + sh_slot(cur));
+    if (first == 0) atomicAdd(reinterpret_cast<unsigned long long*>(w.counters + 32) + 5, (unsigned long long)n);
     int e = 0;
     int2 work = make_int2(0, 0);
-    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    for (int64_t i = first; i < n; i += stride) {
         const float4 o = w.sh_o[i];
         const float4 d = w.sh_d[i];
         const int p = __float_as_int(o.w);
@@ -368,7 +385,28 @@ __global__ void MCEV_TRAV_BOUNDS k_shadow(DevScene sc, DevFrame fr, DevParams P,
     add_work(w, WORK_SHADOW, work);
 }
 
+template <bool kBatch>
+__global__ void MCEV_TRAV_BOUNDS k_shadow(DevScene sc, DevFrame fr, DevParams P, Wave w, int cur, int32_t* err,
+                                          const Job* __restrict__ jobs) {
+    shadow_rays<kBatch>(sc, fr, P, w, cur, err, jobs, blockIdx.x * (int64_t)blockDim.x + threadIdx.x,
+                        (int64_t)gridDim.x * blockDim.x);
+}
 
+// One launch for the shadow rays of bounce d (appended by shade with queue
+// `cur`) and the closest hits of bounce d + 1 (queue 1 - cur): the first
+// `g_ext` blocks extend, the rest trace shadow rays.  Two independent traversal
+// workloads in one grid keep the SMs busy while the other's longest rays finish.
+template <bool kBatch>
+__global__ void MCEV_TRAV_BOUNDS k_shadow_extend(DevScene sc, DevFrame fr, DevParams P, Wave w, int cur,
+                                                 int32_t g_ext, int32_t* err, const Job* __restrict__ jobs) {
+    if ((int32_t)blockIdx.x < g_ext)
+        extend_rays<kBatch>(sc, fr, P.t_min, w, 1 - cur, err, jobs, blockIdx.x * (int64_t)blockDim.x + threadIdx.x,
+                            (int64_t)g_ext * blockDim.x);
+    else
+        shadow_rays<kBatch>(sc, fr, P, w, cur, err, jobs,
+                            (blockIdx.x - g_ext) * (int64_t)blockDim.x + threadIdx.x,
+                            (int64_t)(gridDim.x - g_ext) * blockDim.x);
+}
 
 // ------------------------------------------------------------------ per-pixel statistics + test + requeue + events
 struct Moments {
@@ -603,13 +641,24 @@ cudaError_t launch_shade(const DevScene& sc, const DevFrame& fr, const DevParams
     return cudaGetLastError();
 }
 
-cudaError_t launch_shadow(const DevScene& sc, const DevFrame& fr, const DevParams& P, const Wave& w, int64_t max_n,
-                          int32_t* err, int sms, cudaStream_t st, const Job* jobs) {
+cudaError_t launch_shadow(const DevScene& sc, const DevFrame& fr, const DevParams& P, const Wave& w, int cur,
+                          int64_t max_n, int32_t* err, int sms, cudaStream_t st, const Job* jobs) {
     if (jobs)
-        k_shadow<true><<<grid_for(max_n, MCEV_TRAV_BLOCK, sms, 16), MCEV_TRAV_BLOCK, 0, st>>>(sc, fr, P, w, err, jobs);
+        k_shadow<true><<<grid_for(max_n, MCEV_TRAV_BLOCK, sms, 16), MCEV_TRAV_BLOCK, 0, st>>>(sc, fr, P, w, cur, err,
+                                                                                              jobs);
     else
-        k_shadow<false><<<grid_for(max_n, MCEV_TRAV_BLOCK, sms, 16), MCEV_TRAV_BLOCK, 0, st>>>(sc, fr, P, w, err,
+        k_shadow<false><<<grid_for(max_n, MCEV_TRAV_BLOCK, sms, 16), MCEV_TRAV_BLOCK, 0, st>>>(sc, fr, P, w, cur, err,
                                                                                                nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_shadow_extend(const DevScene& sc, const DevFrame& fr, const DevParams& P, const Wave& w, int cur,
+                                 int64_t max_n, int32_t* err, int sms, cudaStream_t st, const Job* jobs) {
+    const int g = grid_for(max_n, MCEV_TRAV_BLOCK, sms, 16);
+    if (jobs)
+        k_shadow_extend<true><<<2 * g, MCEV_TRAV_BLOCK, 0, st>>>(sc, fr, P, w, cur, g, err, jobs);
+    else
+        k_shadow_extend<false><<<2 * g, MCEV_TRAV_BLOCK, 0, st>>>(sc, fr, P, w, cur, g, err, nullptr);
     return cudaGetLastError();
 }
 

@@ -35,8 +35,11 @@ cudaError_t launch_extend(const DevScene& sc, const DevFrame& fr, float t_min, c
                           int32_t* err, int sms, cudaStream_t st, const Job* jobs);
 cudaError_t launch_shade(const DevScene& sc, const DevFrame& fr, const DevParams& P, const Wave& w, int cur,
                          int64_t max_n, int sms, cudaStream_t st, const Job* jobs);
-cudaError_t launch_shadow(const DevScene& sc, const DevFrame& fr, const DevParams& P, const Wave& w, int64_t max_n,
-                          int32_t* err, int sms, cudaStream_t st, const Job* jobs);
+cudaError_t launch_shadow(const DevScene& sc, const DevFrame& fr, const DevParams& P, const Wave& w, int cur,
+                          int64_t max_n, int32_t* err, int sms, cudaStream_t st, const Job* jobs);
+// shadow rays of the bounce with queue `cur` and closest hits of queue 1 - cur, in one launch
+cudaError_t launch_shadow_extend(const DevScene& sc, const DevFrame& fr, const DevParams& P, const Wave& w, int cur,
+                                 int64_t max_n, int32_t* err, int sms, cudaStream_t st, const Job* jobs);
 cudaError_t launch_stats(const Wave& w, const StatsArgs& A, const int32_t* queue, int64_t j0, int64_t n_pix,
                          int32_t* next_queue, int sms, cudaStream_t st, const Job* jobs);
 // out[i] += (float)acc[i] for i < n (the adjoint's FP64 emission accumulator)
