@@ -117,7 +117,9 @@ typedef struct {
                              are unused.  1 = one batch per round; 0 = library default (16). */
 } mcev_params;
 
-/* kernel classes reported in mcev_stats */
+/* kernel classes reported in mcev_stats.  MCEV_K_EXTEND counts the traversal
+ * launches: closest hits, and the shadow rays a bounce traces in the same
+ * launch as the next bounce's closest hits (MCEV_K_SHADOW then stays 0). */
 enum { MCEV_K_RAYGEN = 0, MCEV_K_EXTEND = 1, MCEV_K_SHADE = 2, MCEV_K_SHADOW = 3, MCEV_K_STATS = 4,
        MCEV_K_CLASSES = 5 };
 
