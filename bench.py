@@ -25,12 +25,13 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "event frames/s and Mpaths/s at 1280x720 vs uniform-spp on same GPU at matched error"
-# ops per BVH node fetch (two ray/box slab tests: 12 plane FMAs, 16 min/max,
-# 2 compares) and per watertight ray/triangle test (9 subtractions, 18 shear
-# FMAs, 9 z terms, 6 edge-function products, 8 sign tests, det, T, divide)
-OPS_PER_NODE = 30
-OPS_PER_TRI = 55
+# Algorithmic work of BVH traversal: 12 FLOP per ray/box slab test (a BVH2
+# node fetch tests two child boxes, 24 FLOP) and 25 FLOP per ray/triangle
+# test, against the FP32 FMA peak of 128 lanes x 2 FLOP per SM per clock
+FLOP_PER_BOX = 12
+FLOP_PER_TRI = 25
 FP32_LANES_PER_SM = 128
+FLOP_PER_LANE_CLOCK = 2
 
 
 def parse():
@@ -48,7 +49,10 @@ def parse():
     ap.add_argument("--no-matched", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--crop", type=int, default=24, help="oracle crop side (pixels)")
+    ap.add_argument("--crop", type=int, default=24,
+                    help="oracle crop side (pixels) of one --impl reference step (the whole run stays within minutes)")
+    ap.add_argument("--cpu-crop", type=int, default=64,
+                    help="oracle crop side (pixels) of the cpu_baseline sample (one frame pair, ~30 s of CPU work)")
     ap.add_argument("--wavefront", type=int, default=0)
     ap.add_argument("--no-tune", action="store_true", help="batch64: skip the autotuner")
     ap.add_argument("--profile-band", type=int, nargs=3, metavar=("ROW0", "ROW1", "SPP"),
@@ -321,6 +325,20 @@ STATS_BYTES_PER_PIXEL_VISIT = 44
 STATS_BYTES_PER_PATH = 4
 QUALITY_BYTES_PER_EVENT = 4
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per traced ray of
+# the traversal launches, from the ncu capture of the terrain band recorded in
+# profiles/; None while the traversal kernels differ from the captured build.
+TRAVERSAL_DRAM_BYTES_PER_RAY = None
+
+
+def traversal_traffic(rays_per_launch: float):
+    """DRAM bytes of an average traversal launch: the captured bytes per ray
+    scaled by the rays an average timed launch traces (traffic grows with the
+    rays, as the captured launches show), or None."""
+    if TRAVERSAL_DRAM_BYTES_PER_RAY is None:
+        return None
+    return TRAVERSAL_DRAM_BYTES_PER_RAY * rays_per_launch
+
 
 def _hbm_peak():
     try:
@@ -381,35 +399,6 @@ def run_quality(args):
             "metrics": {k: q[k] for k in ("rmse", "psnr", "precision", "recall", "f1", "pscd")},
             "clocks": clk}
     print(json.dumps(line), flush=True)
-
-
-def traversal_l1_peak(local: int) -> dict:
-    """Node visits per second of the closest-hit kernel when every node and
-    triangle fetch hits L1: camera inside a closed level-3 icosphere (1,280
-    triangles; BVH + triangles ~80 KB), diffuse bounces to depth 6 so that
-    rays are as incoherent as the terrain's, 1280x720 x 32 uniform samples.
-    Best of 3 frames; the measured ceiling of the traversal loop."""
-    import scenegen as sg
-    from paper_2408_07996_gb300 import UNIFORM
-    from paper_2408_07996_gb300.api import Renderer
-
-    sc = sg.furnace_sphere(0.5, 1.0, level=3)
-    w = sg.Workload("l1_sphere", sc, 1280, 720, [0.0, 1.0], spp_min=32, spp_batch=32, spp_max=32, C=0.2,
-                    alpha=0.05, max_depth=6, nee=0, mis=0)
-    r = Renderer(1280, 720, local)
-    r.upload(w.scene)
-    r.configure(w)
-    r.set_params(variant=UNIFORM, profile=1)
-    best = None
-    for _ in range(3):
-        st = r.render_events(w.times[0], w.times[1], w.C, w.alpha, 32, 32)["stats"]
-        rate = st["nodes_closest"] / (st["kernel_ms"][1] / 1e3)
-        if best is None or rate > best["node_visits_per_s"]:
-            best = {"node_visits_per_s": rate, "rays_per_s": st["rays_closest"] / (st["kernel_ms"][1] / 1e3),
-                    "nodes_per_ray": st["nodes_closest"] / max(1, st["rays_closest"]),
-                    "tris_per_ray": st["tris_closest"] / max(1, st["rays_closest"])}
-    r.close()
-    return best
 
 
 def run_ablation(args):
@@ -610,30 +599,37 @@ def main():
     # rays; a bounce's shadow rays share a launch with the next bounce's
     # closest hits), from the timed steps: device time of the traversal
     # launches (CUDA events on the library's stream) and the traversal work
-    # they did
+    # they did (box and triangle tests counted by the kernels)
     kms = [sum(s["kernel_ms"][i] for s in steps) for i in range(5)]
     kcnt = [sum(s["kernel_count"][i] for s in steps) for i in range(5)]
+    boxes = sum(s["boxes_closest"] + s["boxes_shadow"] for s in steps)
     nodes = sum(s["nodes_closest"] + s["nodes_shadow"] for s in steps)
     tris = sum(s["tris_closest"] + s["tris_shadow"] for s in steps)
     rays = sum(s["rays_closest"] + s["rays_shadow"] for s in steps)
     ext_ms = kms[1] + kms[3]
-    ops = nodes * OPS_PER_NODE + tris * OPS_PER_TRI
+    n_trav = max(1, kcnt[1] + kcnt[3])
+    flop = boxes * FLOP_PER_BOX + tris * FLOP_PER_TRI
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     sm_max_mhz = clk.get("sm_max_mhz") or 2070.0
-    peak_tops = sm_count * FP32_LANES_PER_SM * sm_max_mhz * 1e6 / 1e12
-    achieved_tops = ops / (ext_ms / 1e3) / 1e12 if ext_ms > 0 else None
+    peak_tflops = sm_count * FP32_LANES_PER_SM * FLOP_PER_LANE_CLOCK * sm_max_mhz * 1e6 / 1e12
+    achieved = flop / n_trav / (ext_ms / n_trav / 1e3) / 1e12 if ext_ms > 0 else None
     total_kms = sum(kms)
     roofline = {"kernel": "BVH traversal: k_extend, k_shadow_extend (closest-hit + shadow rays)", "bound": "alu",
-                "achieved": achieved_tops, "peak": peak_tops, "unit": "Tops/s (FP32 lane ops)",
-                "frac": (achieved_tops / peak_tops) if achieved_tops else None, "traffic": None,
-                "avg_launch_ms": ext_ms / max(1, kcnt[1] + kcnt[3]),
-                "ops_per_launch": ops / max(1, kcnt[1] + kcnt[3]),
-                "nodes_per_ray": nodes / max(1, rays),
-                "tris_per_ray": tris / max(1, rays),
+                "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                "frac": (achieved / peak_tflops) if achieved else None,
+                "traffic": traversal_traffic(rays / n_trav),
+                "avg_launch_ms": ext_ms / n_trav, "launches": n_trav,
+                "flop_per_launch": flop / n_trav,
+                "box_tests_per_launch": boxes / n_trav, "tri_tests_per_launch": tris / n_trav,
+                "rays_per_launch": rays / n_trav,
+                "node_fetches_per_ray": nodes / max(1, rays), "box_tests_per_ray": boxes / max(1, rays),
+                "tri_tests_per_ray": tris / max(1, rays),
                 "grays_per_s": rays / (ext_ms / 1e3) / 1e9 if ext_ms else None,
                 "kernel_share": {n: round(kms[i] / total_kms, 4) if total_kms else None
                                  for i, n in enumerate(["raygen", "traversal", "shade", "shadow", "stats"])},
-                "peak_basis": f"{sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_max_mhz:.0f} MHz"}
+                "peak_basis": f"nominal FP32 FMA peak: {sm_count} SMs x {FP32_LANES_PER_SM} lanes x "
+                              f"{FLOP_PER_LANE_CLOCK} FLOP x {sm_max_mhz:.0f} MHz",
+                "work_basis": f"{FLOP_PER_BOX} FLOP per ray/box test, {FLOP_PER_TRI} per ray/triangle test"}
 
     # statistics kernel against HBM
     hbm_peak, hbm_basis = _hbm_peak()
@@ -643,11 +639,6 @@ def main():
                   "unit": "GB/s", "basis": hbm_basis,
                   "frac": stats_bytes / (kms[4] / 1e3) / 1e9 / hbm_peak if kms[4] else None,
                   "bytes_per_frame": stats_bytes / K, "avg_launch_ms": kms[4] / max(1, kcnt[4])}
-    if rank == 0 and not args.no_uniform:
-        pk = traversal_l1_peak(local)
-        roofline["l1_peak"] = {**pk, "scene": "inside a 1,280-triangle icosphere (BVH in L1), depth 6, 1280x720 x 32 spp"}
-        roofline["node_visits_per_s"] = nodes / (ext_ms / 1e3) if ext_ms else None
-        roofline["frac_of_l1_peak"] = roofline["node_visits_per_s"] / pk["node_visits_per_s"] if ext_ms else None
 
     line = {"metric": METRIC, "value": frames_per_s, "unit": "event frames/s", "n_gpus": world, "steps": K,
             "warmup": Wm, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
@@ -731,14 +722,14 @@ def main():
 
     r.close()
     if rank == 0 and world == 1 and not args.no_cpu:
-        run, npix, threads = oracle_sample(w, args.crop, Wm)
+        run, npix, threads = oracle_sample(w, args.cpu_crop, Wm)
         dt, cpaths, cout = run()
         mpps = cpaths / dt / 1e6
         per_px = float(cout["n"].mean())
         line["cpu_baseline"] = {
             "value": mpps * 1e6 / (per_px * w.width * w.height), "unit": "event frames/s", "cores": threads,
             "kind": "oracle", "mpaths_per_s": mpps,
-            "sample": f"FP64 oracle, Alg. 1 on a {args.crop}x{args.crop} centred crop of frame pair "
+            "sample": f"FP64 oracle, Alg. 1 on a {args.cpu_crop}x{args.cpu_crop} centred crop of frame pair "
                       f"{Wm}->{Wm + 1} (reference frame included): {cpaths} paths in {dt:.1f} s; "
                       f"frames/s extrapolated per path to the full frame"}
     if rank == 0:

@@ -134,8 +134,8 @@ typedef struct {
     int64_t pixels_at_cap;  /* pixels that used spp_max samples */
     int64_t nonfinite;      /* path values that were not finite and counted as 0 */
     double gpu_ms;          /* device time of the call (CUDA events) */
-    /* traversal work: BVH nodes fetched (each tests two child boxes) and
-     * ray/triangle tests, for closest-hit and for shadow (any-hit) rays */
+    /* traversal work: BVH nodes fetched and ray/triangle tests, for
+     * closest-hit and for shadow (any-hit) rays (ray/box tests below) */
     int64_t nodes_closest, tris_closest, nodes_shadow, tris_shadow;
     int64_t rays_closest, rays_shadow;
     /* per kernel class (MCEV_K_*): launches, and summed device time in ms
@@ -145,6 +145,8 @@ typedef struct {
     double kernel_ms[MCEV_K_CLASSES];
     int64_t h2d_bytes, d2h_bytes;   /* host<->device copies made by the call */
     int64_t stats_pixels;   /* pixel visits of the statistics kernel (sum over its launches) */
+    int64_t boxes_closest, boxes_shadow;  /* ray/box slab tests of the traversals (a two-wide node
+                                             fetch tests 2 boxes, a wide node one per child) */
 } mcev_stats;
 
 /* Creates a context on CUDA device `device` for width x height images.
@@ -348,15 +350,23 @@ typedef struct {
     size_t err_len;
 } mcev_detect_args;
 
-/* Runs one batch of the detector without allocating: merges each listed
- * pixel's spp_r samples y = ln(L + eps) into its running statistics, tests
- * it once it has spp_min samples (a test is done at every sample count
- * spp_min + r * spp_batch below spp_max), and either lists it in `undecided`
- * or writes its event, sample count and mean (updating the reference on an
- * event).  *n_undecided (host) receives the number of pixels listed.
- * Errors: MCEV_ERR_ARG for null or inconsistent arguments, and for
- * schedules needing more than MCEV_DETECT_STATIC_MAX_TESTS tests (the table
- * would not fit the fixed scratch); MCEV_ERR_CUDA for failed CUDA calls. */
+/* Runs the detector on one window of samples without allocating: merges
+ * each listed pixel's spp_r samples y = ln(L + eps) into its running
+ * statistics one batch at a time, tests it at every sample count
+ * spp_min + r * spp_batch below spp_max that the window reaches, and either
+ * lists it in `undecided` or writes its event, sample count and mean
+ * (updating the reference on an event); samples after a pixel's decision are
+ * ignored.  The schedule is enforced: the first call of a frame has
+ * k_base = 0 and spp_r = spp_min; every later call starts on the schedule
+ * (k_base = spp_min + r * spp_batch) and covers whole batches (spp_r a
+ * multiple of spp_batch, or ending exactly at spp_max).  Pixel ids outside
+ * [0, n_total) are skipped, the other pixels are still processed, and the
+ * call then returns MCEV_ERR_ARG.  *n_undecided (host) receives the number
+ * of pixels listed.
+ * Errors: MCEV_ERR_ARG for null or inconsistent arguments, calls off the
+ * schedule, out-of-range pixel ids, and schedules needing more than
+ * MCEV_DETECT_STATIC_MAX_TESTS tests (the table would not fit the fixed
+ * scratch); MCEV_ERR_CUDA for failed CUDA calls. */
 mcev_status mcev_detect_batch_static(const mcev_detect_args* args, int64_t* n_undecided);
 
 /* ------------------------------------------------------------------------

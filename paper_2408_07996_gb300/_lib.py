@@ -55,6 +55,7 @@ class Stats(C.Structure):
         ("tris_shadow", C.c_int64), ("rays_closest", C.c_int64), ("rays_shadow", C.c_int64),
         ("kernel_count", C.c_int32 * 5), ("reserved", C.c_int32), ("kernel_ms", C.c_double * 5),
         ("h2d_bytes", C.c_int64), ("d2h_bytes", C.c_int64), ("stats_pixels", C.c_int64),
+        ("boxes_closest", C.c_int64), ("boxes_shadow", C.c_int64),
     ]
 
     def as_dict(self):

@@ -906,6 +906,8 @@ mcev_status fill_stats(mcev_ctx* ctx, mcev_stats* stats_out, int64_t paths, int6
     stats_out->h2d_bytes = ctx->h2d;
     stats_out->stats_pixels = ctx->stats_pix;
     stats_out->d2h_bytes = ctx->d2h;
+    stats_out->boxes_closest = (int64_t)u[7];
+    stats_out->boxes_shadow = (int64_t)u[8];
     if (c[15]) return fail(ctx, MCEV_ERR_STATE, "traversal stack overflow");
     return MCEV_OK;
 }

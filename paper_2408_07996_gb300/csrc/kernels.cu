@@ -90,7 +90,8 @@ __global__ void __launch_bounds__(256) k_raygen(DevFrame fr, DevParams P, Wave w
     }
 }
 
-// traversal work counters: 64-bit (nodes, tris) pairs after the int32 counters
+// traversal work counters: 64-bit (nodes, tris) pairs after the int32
+// counters, and the ray/box tests (two per node fetch of the two-wide BVH)
 enum { WORK_CLOSEST = 0, WORK_SHADOW = 1 };
 __device__ __forceinline__ void add_work(const Wave& w, int which, int2 work) {
     const unsigned m = __activemask();
@@ -100,6 +101,7 @@ __device__ __forceinline__ void add_work(const Wave& w, int which, int2 work) {
         unsigned long long* c = reinterpret_cast<unsigned long long*>(w.counters + 32);
         atomicAdd(c + 2 * which, (unsigned long long)nodes);
         atomicAdd(c + 2 * which + 1, (unsigned long long)tris);
+        atomicAdd(c + 7 + which, 2ull * (unsigned long long)nodes);
     }
 }
 
@@ -716,9 +718,9 @@ cudaError_t launch_iota(int32_t* q, int64_t n, int sms, cudaStream_t st) {
 }  // namespace mcev
 
 // ------------------------------------------------------------------ allocation-free detector step
-// Scratch of mcev_detect_batch_static: int32 counters [0, 256) (the layout
-// k_stats expects: [3] re-queue count, [4] non-finite, [5]/[6] events +/-,
-// [7] pixels at the cap) followed by the critical-t table.  It lives in the
+// Scratch of mcev_detect_batch_static: int32 counters [0, 256) in the layout
+// of Wave::counters (layout.h lists every slot; k_stats uses [3]-[8] and the
+// uint64 word [32 + 6]) followed by the critical-t table.  It lives in the
 // library image so the call never allocates; host code reaches it only
 // through the address cudaGetSymbolAddress returns for the current device.
 static __device__ __align__(256) unsigned char g_detect_scratch[MCEV_DETECT_STATIC_SCRATCH_BYTES];
@@ -757,6 +759,15 @@ extern "C" mcev_status mcev_detect_batch_static(const mcev_detect_args* a, int64
         !(a->alpha > 0.0f && a->alpha < 1.0f) || a->variant < 0 || a->variant > 3 || a->se_mode < 0 ||
         a->se_mode > 1 || (int64_t)a->n_pix * a->spp_r > ((int64_t)1 << 40))
         return static_fail(a, MCEV_ERR_ARG, "mcev_detect_batch_static: inconsistent sizes or settings");
+    // Later calls must start on the test schedule spp_min + r * spp_batch and
+    // cover whole batches (only the last batch of the frame may be shorter, as
+    // it ends at spp_max), so that the kernel tests at every schedule point the
+    // window crosses and each test reads the critical value of its own count.
+    if (a->k_base > 0 && (a->k_base < a->spp_min || (a->k_base - a->spp_min) % a->spp_batch != 0 ||
+                          (a->spp_r % a->spp_batch != 0 && a->k_base + a->spp_r != a->spp_max)))
+        return static_fail(a, MCEV_ERR_ARG,
+                           "mcev_detect_batch_static: call off the test schedule: k_base must be spp_min + r * "
+                           "spp_batch and spp_r a multiple of spp_batch (or end at spp_max)");
     const int64_t n_tests = (a->spp_max - a->spp_min + a->spp_batch - 1) / a->spp_batch;
     if (n_tests > MCEV_DETECT_STATIC_MAX_TESTS)
         return static_fail(a, MCEV_ERR_ARG,
@@ -817,7 +828,9 @@ extern "C" mcev_status mcev_detect_batch_static(const mcev_detect_args* a, int64
     A.eps = a->eps;
     A.C = a->C;
     A.spp_r = a->spp_r;
-    A.sub = a->spp_r;
+    // the first call is the first batch (spp_min samples, one test at its
+    // end); a later call's samples are merged and tested one spp_batch at a time
+    A.sub = a->k_base == 0 ? a->spp_r : a->spp_batch;
     A.k_base = a->k_base;
     A.spp_min = a->spp_min;
     A.spp_batch = a->spp_batch;

@@ -44,12 +44,37 @@ struct Node {
     int4 d;
 };
 
+// Compressed 8-wide node (80 B, five 16-byte words): child boxes on a grid of
+// step 2^(e_a - 127) per axis a anchored at (px, py, pz); child slot i spans
+// [p + qlo[i] * step, p + qhi[i] * step] per axis (empty slots: qlo > qhi).
+//   e_imask : e_x | e_y << 8 | e_z << 16 | imask << 24  (imask bit i: slot i
+//             is an internal node)
+//   child_base: first child node; internal children are stored contiguously
+//             in slot order, so slot i's node is child_base + popc(imask below i)
+//   tri_base : bits 0..28 first triangle of the leaf children (contiguous);
+//             bits 29..31 number of non-empty slots - 1
+//   meta[i]  : internal: 0x20 | (24 + i); leaf: (2^count - 1) << 5 | offset of
+//             its first triangle from tri_base (count 1..3, offsets < 24);
+//             empty: 0.  (meta >> 5) << (meta & 31) is the slot's bit in a
+//             hit mask whose bits 24..31 are internal children, 0..23 triangles.
+struct Node8 {
+    float px, py, pz;
+    uint32_t e_imask;
+    uint32_t child_base, tri_base;
+    uint32_t meta[2];
+    uint32_t qlo_x[2], qlo_y[2], qlo_z[2], qhi_x[2];
+    uint32_t qhi_y[2], qhi_z[2];
+};
+static_assert(sizeof(Node8) == 80, "wide node is five 16-byte words");
+
 enum { MAT_DIFFUSE = 0, MAT_GGX = 1 };
 // material type word: low byte = BSDF, bit 8 = albedo from the texture
 enum { MAT_TEXTURED = 0x100 };
 
 struct DevScene {
-    const Node* nodes;        // BLAS nodes of every mesh
+    const Node* nodes;        // BLAS nodes of every mesh (two-wide layout)
+    const uint4* wnodes;      // BLAS nodes of every mesh (compressed 8-wide layout: 5 uint4 per node)
+    int32_t wide;             // 1: the BLAS roots index `wnodes`
     const float4* tris;       // 3 float4 per triangle, leaf order
     const float4* mats;       // (type, albedo, rough, emit)
     const float* env;         // [eh][ew] radiance
@@ -115,8 +140,19 @@ struct Wave {
     int32_t* sh_m;            // adjoint: material of the sampled light (-1: environment)
     float* Ltot;              // adjoint: radiance of each path from the first pass
     float* delta;             // adjoint: d loss / d L of each path
-    // device counters: [0],[1] ray queue sizes, [2] shadow count, [3] pixel queue
-    // size, [4] non-finite path values, [5] events +, [6] events -, [7] at cap
+    // Device counters, 64 int32 words; every slot the kernels use:
+    //   [0], [1]  ray queue sizes (ping-pong queues 0 and 1)
+    //   [2], [19] shadow-ray counts of the bounces traced from ray queue 0 / 1
+    //   [3]       undecided pixels re-queued by the statistics kernel
+    //   [4]       non-finite path values (counted as 0)
+    //   [5], [6]  positive / negative events
+    //   [7]       pixels decided at spp_max
+    //   [8]       caller pixel id outside [0, n_total) (allocation-free step)
+    //   [15]      traversal stack overflow
+    //   from [32] on, uint64 words: [0] nodes and [1] triangles of closest-hit
+    //   traversal, [2] nodes and [3] triangles of shadow rays, [4] closest-hit
+    //   rays, [5] shadow rays, [6] samples that entered decisions, [7] and
+    //   [8] ray/box tests of closest-hit and shadow traversal
     int32_t* counters;
     int64_t cap;
 };

@@ -10,19 +10,26 @@ import torch
 
 import oracle as O
 import scenegen as sg
-from parity import per_sample, renderer_for, summary
+from parity import (T_BAND, C_BAND, frame_mismatches, in_band, per_sample, renderer_for, summary,
+                    topology_ok, worst_sample)
 
 pytestmark = pytest.mark.gpu
 
 MEAN_TOL = 1e-4      # per-pixel mean ln L, absolute
-T_BAND = 1e-3        # |t - t_crit| band where FP32/FP64 decisions may differ
-C_BAND = 1e-5        # | |gap| - C | band
+# T_BAND = 1e-3: |t - t_crit| band where FP32/FP64 decisions may differ;
+# C_BAND = 1e-5: | |gap| - C | band (tests/parity.py)
 SAMPLE_MISMATCH = 2e-3   # max fraction of samples with different discrete decisions
-# Per-sample ln L on samples with identical decisions: FP32 paths have heavy
-# but rare tails (grazing cosines, near-polar environment directions), so the
-# bar is on the 99.9th percentile, with a loose cap on the maximum.
+# Per-sample ln L on samples with identical decisions: the 99.9th percentile
+# within 1e-4 and every sample within 1e-3 (measured maxima: Cornell box
+# 4.3e-4, terrain 1.3e-4).  The sphere field's bar is 2e-3 (measured maximum
+# 1.27e-3): its never-moving spheres are baked to world space in FP32, which
+# tilts a facet normal by up to ~6e-6 rad (vertex rounding ~2e-7 on 0.045-unit
+# edges 5 units from the origin), and where next-event estimation picks a sun
+# direction at grazing incidence (cosine 1.7e-3 .. 4e-3) that is a relative
+# error of 1e-3 .. 2e-3 in the cosine factor of the contribution.
 SAMPLE_P999 = 1e-4
-SAMPLE_MAX = 1e-2
+SAMPLE_MAX = 1e-3
+SAMPLE_MAX_BAKED_GRAZING = 2e-3
 
 
 @pytest.fixture(scope="module")
@@ -67,7 +74,7 @@ def test_cornell_per_sample_parity(cornell, t):
     pix = np.arange(0, 4096, 3)                  # 1366 pixels
     ps = per_sample(r, osc, O.params_of(w), t, pix, 5, 37, w.eps)
     s = summary(ps)
-    print("cornell per-sample", t, s)
+    print("cornell per-sample", t, s, worst_sample(ps, pix, 5))
     assert s["mismatch"] <= SAMPLE_MISMATCH
     assert s["p999_dy"] < SAMPLE_P999 and s["max_dy"] < SAMPLE_MAX
     # per-pixel means over pixels whose every sample made the same decisions
@@ -139,7 +146,12 @@ def test_cornell_variant_parity(cornell, variant):
 
 
 def test_second_frame_reuses_reference(cornell):
-    # frames (0,1) then (1,2): the reference carried over equals the oracle's
+    """Frames (0, 1) then (1, 2): the Alg. 1 frame loop with the reference
+    carried from frame to frame, element by element against the oracle.  A
+    pixel is set aside only when a sample it used at t = 0, 1 or 2 made a
+    different discrete decision in FP32 and FP64, or when either frame's
+    decision lay in a threshold band (the frame-1 decision picks the
+    reference that frame 2 compares against)."""
     w, osc = cornell
     sc = sg.cornell_box(shift=0.02)
     sc3 = sg.Scene(sc.vertices, sc.triangles, sc.tri_material, sc.mesh_ranges, sc.inst_mesh,
@@ -154,15 +166,26 @@ def test_second_frame_reuses_reference(cornell):
     r = renderer_for(w3)
     p, det = O.params_of(w3), O.detect_of(w3)
     pix = np.arange(w3.width * w3.height, dtype=np.int32)
-    r.render_events(0.0, 1.0, w3.C, w3.alpha, w3.spp_batch, w3.spp_max)
+    out1 = r.render_events(0.0, 1.0, w3.C, w3.alpha, w3.spp_batch, w3.spp_max)
+    g1 = {k: out1[k].cpu().numpy().reshape(-1) for k in ("events", "spp", "mean")}
     o1 = O.render_events(osc3, p, det, 0.0, 1.0, pix)
     out2 = r.render_events(1.0, 2.0, w3.C, w3.alpha, w3.spp_batch, w3.spp_max)
     assert out2["stats"]["ref_paths"] == 0
+    g2 = {k: out2[k].cpu().numpy().reshape(-1) for k in ("events", "spp", "mean")}
     o2 = O.render_events(osc3, p, det, 1.0, 2.0, pix, ref=o1["ref"])
-    ev = out2["events"].cpu().numpy().reshape(-1)
-    band = (o2["margin_t"] < T_BAND) | (o2["margin_c"] < C_BAND) | (o1["margin_t"] < T_BAND) | (o1["margin_c"] < C_BAND)
-    agree = (ev == o2["events"]) | band
-    assert agree.mean() > 0.97
+    topo = (topology_ok(r, osc3, p, 0.0, pix, np.full(pix.size, w3.spp_max), w3.eps)
+            & topology_ok(r, osc3, p, 1.0, pix, np.maximum(g1["spp"], o1["n"]), w3.eps)
+            & topology_ok(r, osc3, p, 2.0, pix, np.maximum(g2["spp"], o2["n"]), w3.eps))
+    keep = topo & ~in_band(o1) & ~in_band(o2)
+    f1 = frame_mismatches(g1["events"], g1["spp"], g1["mean"], o1, keep, MEAN_TOL)
+    f2 = frame_mismatches(g2["events"], g2["spp"], g2["mean"], o2, keep, MEAN_TOL)
+    print("carried reference: kept %d of %d; frame 1 %s; frame 2 %s; events %d/%d" % (
+        keep.sum(), pix.size, f1, f2, (g2["events"] != 0).sum(), (o2["events"] != 0).sum()))
+    assert f1["bad_ev"] == 0 and f1["bad_n"] == 0 and f1["mean_ok"]
+    assert f2["bad_ev"] == 0 and f2["bad_n"] == 0 and f2["mean_ok"]
+    q = SAMPLE_MISMATCH
+    assert 1 - topo.mean() <= 1 - (1 - q) ** (4 * w3.spp_max)
+    assert keep.mean() > 0.8 and (o2["events"][keep] != 0).sum() > 50
     r.close()
 
 
@@ -236,9 +259,9 @@ def test_spheres_per_sample_parity(spheres, k):
     pix = np.sort(rng.choice(w.width * w.height, size=1500, replace=False))
     ps = per_sample(r, osc, O.params_of(w), w.times[k], pix, 0, 24, w.eps)
     s = summary(ps)
-    print("spheres per-sample", k, s)
+    print("spheres per-sample", k, s, worst_sample(ps, pix, 0))
     assert s["mismatch"] <= SAMPLE_MISMATCH
-    assert s["p999_dy"] < SAMPLE_P999 and s["max_dy"] < SAMPLE_MAX
+    assert s["p999_dy"] < SAMPLE_P999 and s["max_dy"] < SAMPLE_MAX_BAKED_GRAZING
     full = ps["match"].all(axis=1)
     assert np.abs(ps["yg"].mean(1) - ps["yo"].mean(1))[full].max() < MEAN_TOL
     r.close()
@@ -251,7 +274,7 @@ def test_terrain_per_sample_parity(terrain):
     pix = np.sort(rng.choice(w.width * w.height, size=1200, replace=False))
     ps = per_sample(r, osc, O.params_of(w), w.times[3], pix, 100, 16, w.eps)
     s = summary(ps)
-    print("terrain per-sample", s)
+    print("terrain per-sample", s, worst_sample(ps, pix, 100))
     assert s["mismatch"] <= SAMPLE_MISMATCH
     assert s["p999_dy"] < SAMPLE_P999 and s["max_dy"] < SAMPLE_MAX
     full = ps["match"].all(axis=1)
