@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--cpu-crop", type=int, default=64,
                     help="oracle crop side (pixels) of the cpu_baseline sample (one frame pair, ~30 s of CPU work)")
     ap.add_argument("--wavefront", type=int, default=0)
+    ap.add_argument("--bvh-width", type=int, default=0, choices=[0, 2, 8],
+                    help="BVH node layout (0: the library default)")
     ap.add_argument("--no-tune", action="store_true", help="batch64: skip the autotuner")
     ap.add_argument("--profile-band", type=int, nargs=3, metavar=("ROW0", "ROW1", "SPP"),
                     help="only trace SPP samples of every pixel in image rows [ROW0, ROW1) at keyframe 3 "
@@ -72,7 +74,7 @@ def profile_band(args):
     r = Renderer(w.width, w.height, 0)
     r.upload(w.scene)
     r.configure(w)
-    r.set_params(wavefront=args.wavefront)
+    r.set_params(wavefront=args.wavefront, bvh_width=args.bvh_width)
     r0, r1, spp = args.profile_band
     pix = torch.arange(r0 * w.width, r1 * w.width, dtype=torch.int32, device="cuda")
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -230,8 +232,8 @@ def _config(w):
 def run_batch(args):
     """64 independent frame pairs (image sizes from 128x128 to 640x480,
     5k-100k triangles each) rendered in shared rounds; one step = one event
-    frame of every job.  The wavefront width, batch window and BVH leaf size
-    are picked by the autotuner on the first frame pair after warm-up."""
+    frame of every job.  The BVH node layout and leaf size are picked by the
+    autotuner on the first frame pair after warm-up."""
     import torch
 
     import scenegen as sg
@@ -263,7 +265,7 @@ def run_batch(args):
     tune = None
     if not args.no_tune:
         tune = tune_batch(runner, rs, (times[Wm], times[Wm + 1]), sched,
-                          wavefronts=(1 << 24, 1 << 25), windows=(16,), leaf_sizes=(2, 4))
+                          wavefronts=(1 << 25,), windows=(16,), leaf_sizes=(2, 4), bvh_widths=(2, 8))
         tune = {"best": tune["best"], "trials": len(tune["trials"]), "jobs": len(rs)}
     torch.cuda.synchronize()
     clocks = Clocks(0)
@@ -553,7 +555,7 @@ def main():
     r = Renderer(w.width, w.height, local)
     r.upload(w.scene)
     r.configure(w)
-    r.set_params(profile=1, wavefront=args.wavefront)
+    r.set_params(profile=1, wavefront=args.wavefront, bvh_width=args.bvh_width)
     H, Wd = w.height, w.width
     dev = torch.device("cuda", local)
     out = dict(events=torch.empty((H, Wd), dtype=torch.int8, device=dev),

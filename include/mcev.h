@@ -115,6 +115,10 @@ typedef struct {
                              spp_batch per undecided pixel at once (as many as fill the wavefront),
                              merging and testing them in order; samples after a pixel's decision
                              are unused.  1 = one batch per round; 0 = library default (16). */
+    int32_t bvh_width;  /* node layout of the per-mesh BVHs: 2 (two children per node) or 8
+                           (compressed 8-wide nodes with 8-bit child boxes); 0 = library default.
+                           Changing it rebuilds the BVHs of an uploaded scene.  Results are the
+                           same up to rare FP32 box-culling decisions near a ray's origin. */
 } mcev_params;
 
 /* kernel classes reported in mcev_stats.  MCEV_K_EXTEND counts the traversal
@@ -181,7 +185,9 @@ mcev_status mcev_scene_upload(mcev_ctx* ctx, const mcev_scene_desc* desc);
  * triangles.  Errors: ARG, STATE (no scene), OOM, CUDA. */
 mcev_status mcev_build_bvh(mcev_ctx* ctx, int32_t sah_bins, int32_t max_leaf);
 
-/* Sets render settings (see mcev_params).  Errors: ARG. */
+/* Sets render settings (see mcev_params); a new bvh_width rebuilds the BVHs of
+ * the uploaded scene.  Errors: ARG (the settings are unchanged), and OOM or
+ * CUDA from that rebuild (the scene must then be uploaded again). */
 mcev_status mcev_set_params(mcev_ctx* ctx, const mcev_params* params);
 
 /* First frame of Alg. 1: renders every pixel at time t0 with spp samples and
@@ -264,7 +270,7 @@ typedef struct {
  * first, also batched.  The runner context (which may also be one of the
  * jobs' contexts) supplies the stream, allocator, wavefront buffers and the
  * reported counters.  All jobs must share spp_min, variant and se_mode (the
- * schedule); every other setting is per job.  Jobs must use distinct
+ * schedule) and the BVH node layout (bvh_width); every other setting is per job.  Jobs must use distinct
  * contexts on the runner's device, of at most 2^24 pixels each; n_jobs is
  * 1..256.  Errors: ARG, STATE, OOM, CUDA. */
 mcev_status mcev_render_events_batch(mcev_ctx* runner, const mcev_job* jobs, int32_t n_jobs, float C, float alpha,

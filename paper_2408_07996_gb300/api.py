@@ -36,6 +36,7 @@ class RenderSettings:
     wavefront: int = 0
     profile: int = 0
     batch_window: int = 0
+    bvh_width: int = 0
 
 
 class Renderer:
@@ -154,7 +155,7 @@ class Renderer:
         s = replace(self.settings, **kw)
         p = L.Params(eps=s.eps, t_min=s.t_min, max_depth=s.max_depth, nee=s.nee, mis=s.mis,
                      spp_min=s.spp_min, variant=s.variant, se_mode=s.se_mode, seed=s.seed,
-                     wavefront=s.wavefront, profile=s.profile, batch_window=s.batch_window)
+                     wavefront=s.wavefront, profile=s.profile, batch_window=s.batch_window, bvh_width=s.bvh_width)
         L.check(self.lib.mcev_set_params(self.ctx, C.byref(p)), self.ctx, "mcev_set_params")
         self.settings = s
         return s

@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libmcev.so")
-SOURCES = ["kernels.cu", "quality.cu", "api.cpp", "bvh.cpp", "tdist.cpp"]
+SOURCES = ["kernels.cu", "quality.cu", "api.cpp", "bvh.cpp", "bvh8.cpp", "tdist.cpp"]
 HEADERS = ["layout.h", "device.cuh", "kernels.h", "quality.h", "bvh.h", "tdist.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -24,6 +24,11 @@
 
 using namespace mcev;
 
+// BVH node layout used unless mcev_params.bvh_width asks for the other
+#ifndef MCEV_DEFAULT_BVH_WIDTH
+#define MCEV_DEFAULT_BVH_WIDTH 2
+#endif
+
 namespace {
 
 struct DevBuf {
@@ -84,6 +89,7 @@ struct mcev_ctx {
     bool env_ok = false;
     int sah_bins = 32, max_leaf = 4;
     int bvh_depth = 0;
+    int bvh_width = MCEV_DEFAULT_BVH_WIDTH; // BLAS layout: 2 (two-wide nodes) or 8 (compressed wide)
     std::vector<float> tri_uv;              // [tri][6] texture coordinates (empty: no uvs)
     std::vector<char> inst_static;          // keyframes never change
     std::vector<float> static_vtx;          // world-space triangles of static instances
@@ -94,7 +100,7 @@ struct mcev_ctx {
     // device scene
     DevBuf d_quality;                       // event-quality scratch: two int32 volumes + accumulators
     DevBuf d_gemit;                         // FP64 emission-gradient accumulator of mcev_backward
-    DevBuf d_nodes, d_tris, d_uv, d_mats, d_env, d_marg, d_cond, d_tpdf;
+    DevBuf d_nodes, d_wnodes, d_tris, d_uv, d_mats, d_env, d_marg, d_cond, d_tpdf;
     DevScene dsc{};
     Frame frames[2];
 
@@ -273,8 +279,8 @@ struct TriSrc {
 const float* tri_uv_of(const mcev_ctx* ctx, int64_t prim);
 
 mcev_status build_one(mcev_ctx* ctx, const std::vector<TriSrc>& src, std::vector<Node>& nodes,
-                      std::vector<float4>& tris, std::vector<float2>& uvs, int& root, float lo_out[3],
-                      float hi_out[3], int& depth) {
+                      std::vector<Node8>& wnodes, std::vector<float4>& tris, std::vector<float2>& uvs, int& root,
+                      float lo_out[3], float hi_out[3], int& depth) {
     const int n = (int)src.size();
     std::vector<float> lo(3 * (size_t)n), hi(3 * (size_t)n), ce(3 * (size_t)n);
     for (int i = 0; i < n; ++i) {
@@ -286,23 +292,41 @@ mcev_status build_one(mcev_ctx* ctx, const std::vector<TriSrc>& src, std::vector
         }
     }
     BuiltBvh b = build_bvh(lo.data(), hi.data(), ce.data(), n, ctx->sah_bins, ctx->max_leaf);
-    depth = std::max(depth, b.depth);
-    const int node_off = (int)nodes.size();
     const int64_t tri_off = (int64_t)tris.size() / 3;
-    root = node_off;
-    for (Node nd : b.nodes) {
-        if (nd.d.x >= 0) nd.d.x += node_off;
-        else nd.d.x = ~(int)(tri_off + ~nd.d.x);
-        if (nd.d.y >= 0) nd.d.y += node_off;
-        else nd.d.y = ~(int)(tri_off + ~nd.d.y);
-        nodes.push_back(nd);
+    const std::vector<int>* leaf_order = &b.order;
+    WideBvh wb;
+    if (ctx->bvh_width == 8) {
+        // the binary tree collapsed into compressed 8-wide nodes; the
+        // triangles follow the wide leaves' order
+        wb = collapse_wide(b, lo.data(), hi.data());
+        if (!wb.ok) return fail(ctx, MCEV_ERR_STATE, "internal: wide BVH invariant violated");
+        depth = std::max(depth, wb.depth);
+        const uint32_t node_off = (uint32_t)wnodes.size();
+        root = (int)node_off;
+        for (Node8 nd : wb.nodes) {
+            nd.child_base += node_off;
+            nd.tri_base = (nd.tri_base & 0xE0000000u) | ((nd.tri_base & 0x1FFFFFFFu) + (uint32_t)tri_off);
+            wnodes.push_back(nd);
+        }
+        leaf_order = &wb.tri_order;
+    } else {
+        depth = std::max(depth, b.depth);
+        const int node_off = (int)nodes.size();
+        root = node_off;
+        for (Node nd : b.nodes) {
+            if (nd.d.x >= 0) nd.d.x += node_off;
+            else nd.d.x = ~(int)(tri_off + ~nd.d.x);
+            if (nd.d.y >= 0) nd.d.y += node_off;
+            else nd.d.y = ~(int)(tri_off + ~nd.d.y);
+            nodes.push_back(nd);
+        }
     }
     for (int k = 0; k < 3; ++k) {
         lo_out[k] = std::numeric_limits<float>::max();
         hi_out[k] = -std::numeric_limits<float>::max();
     }
     for (int i = 0; i < n; ++i) {
-        const TriSrc& s = src[b.order[i]];
+        const TriSrc& s = src[(*leaf_order)[i]];
         const float* v = s.v;
         float4 t0, t1, t2;
         t0.x = v[0]; t0.y = v[1]; t0.z = v[2];
@@ -326,6 +350,7 @@ mcev_status build_one(mcev_ctx* ctx, const std::vector<TriSrc>& src, std::vector
 
 mcev_status build_blas(mcev_ctx* ctx) {
     std::vector<Node> nodes;
+    std::vector<Node8> wnodes;
     std::vector<float4> tris;
     std::vector<float2> uvs;
     tris.reserve(ctx->vtx.size() / 3);
@@ -349,7 +374,7 @@ mcev_status build_blas(mcev_ctx* ctx) {
             const int64_t prim = m.first_tri + t;
             src[t] = TriSrc{&ctx->vtx[9 * (size_t)prim], (int32_t)prim, ctx->tri_mat[prim], -1};
         }
-        ST(build_one(ctx, src, nodes, tris, uvs, m.root, m.lo, m.hi, depth));
+        ST(build_one(ctx, src, nodes, wnodes, tris, uvs, m.root, m.lo, m.hi, depth));
     }
     // merged static geometry in world space (keyframe 0 transform, FP64 -> FP32)
     ctx->static_vtx.clear();
@@ -387,21 +412,29 @@ mcev_status build_blas(mcev_ctx* ctx) {
     ctx->static_root = -1;
     ctx->has_static = n_static_tris > 0;
     if (ctx->has_static)
-        ST(build_one(ctx, ssrc, nodes, tris, uvs, ctx->static_root, ctx->static_lo, ctx->static_hi, depth));
+        ST(build_one(ctx, ssrc, nodes, wnodes, tris, uvs, ctx->static_root, ctx->static_lo, ctx->static_hi, depth));
     if (nodes.empty()) {
         Node none;
         std::memset(&none, 0, sizeof none);
         nodes.push_back(none);
+    }
+    if (wnodes.empty()) {
+        Node8 none;
+        std::memset(&none, 0, sizeof none);
+        wnodes.push_back(none);
     }
     if (tris.empty()) {
         tris.push_back(make_float4(0, 0, 0, 0));
         uvs.push_back(make_float2(0, 0));
     }
     // a traversal pushes at most one entry per inner-node level
-    if (depth > MCEV_STACK_HOST)
-        return fail(ctx, MCEV_ERR_ARG, "BVH depth %d exceeds the traversal stack (%d)", depth, MCEV_STACK_HOST);
+    const int cap = ctx->bvh_width == 8 ? MCEV_WSTACK_HOST : MCEV_STACK_HOST;
+    if (depth > cap) return fail(ctx, MCEV_ERR_ARG, "BVH depth %d exceeds the traversal stack (%d)", depth, cap);
     ctx->bvh_depth = depth;
     ST(upload(ctx, ctx->d_nodes, nodes.data(), nodes.size() * sizeof(Node)));
+    ST(upload(ctx, ctx->d_wnodes, wnodes.data(), wnodes.size() * sizeof(Node8)));
+    ctx->dsc.wnodes = (const uint4*)ctx->d_wnodes.ptr;
+    ctx->dsc.wide = ctx->bvh_width == 8 ? 1 : 0;
     ST(upload(ctx, ctx->d_tris, tris.data(), tris.size() * sizeof(float4)));
     ctx->dsc.nodes = (const Node*)ctx->d_nodes.ptr;
     ctx->dsc.tris = (const float4*)ctx->d_tris.ptr;
@@ -542,7 +575,8 @@ mcev_status frame_setup(mcev_ctx* ctx, double t, int slot) {
             if (nd.d.x < 0 && nd.d.z > 0) nd.d.x = ~b.order[~nd.d.x];
             if (nd.d.y < 0 && nd.d.w > 0) nd.d.y = ~b.order[~nd.d.y];
         }
-        if (b.depth + ctx->bvh_depth > MCEV_STACK_HOST)
+        // the two-wide BLAS continue on the TLAS stack; wide BLAS have their own
+        if (b.depth + (ctx->bvh_width == 8 ? 0 : ctx->bvh_depth) > MCEV_STACK_HOST)
             return fail(ctx, MCEV_ERR_ARG, "TLAS + BLAS depth exceeds the traversal stack (%d)", MCEV_STACK_HOST);
     }
     // emitters in world space
@@ -762,6 +796,7 @@ struct BatchRun {
     int64_t q0 = 0;
     int32_t max_depth = 0;
     bool any_nee = false;
+    bool wide = false;        // every job's BLAS use the wide layout
 };
 
 // one chunk of n_paths = nj * spp_r paths through every bounce
@@ -772,9 +807,11 @@ mcev_status trace_chunk(mcev_ctx* ctx, const Frame& fr, const DevParams& P, cons
     const Job* jobs = B ? B->d_jobs : nullptr;
     const int depth_max = B ? B->max_depth : P.max_depth;
     const bool nee = B ? B->any_nee : P.nee != 0;
+    const bool wide = B ? B->wide : ctx->dsc.wide != 0;
     LAUNCH(MCEV_K_RAYGEN, launch_raygen(fr.dev, P, w, queue, j0, spp_r, k_base, n_paths, 0, ctx->sms, ctx->stream, jobs));
     int cur = 0;
-    LAUNCH(MCEV_K_EXTEND, launch_extend(ctx->dsc, fr.dev, P.t_min, w, cur, n_paths, err, ctx->sms, ctx->stream, jobs));
+    LAUNCH(MCEV_K_EXTEND,
+           launch_extend(ctx->dsc, fr.dev, P.t_min, w, cur, n_paths, err, ctx->sms, ctx->stream, jobs, wide));
     for (int depth = 0; depth <= depth_max; ++depth) {
         LAUNCH(MCEV_K_SHADE, launch_shade(ctx->dsc, fr.dev, P, w, cur, n_paths, ctx->sms, ctx->stream, jobs));
         if (depth < depth_max) {
@@ -782,16 +819,16 @@ mcev_status trace_chunk(mcev_ctx* ctx, const Frame& fr, const DevParams& P, cons
             // this bounce's shadow rays and the next bounce's closest hits in one launch
             if (nee)
                 LAUNCH(MCEV_K_EXTEND, launch_shadow_extend(ctx->dsc, fr.dev, P, w, cur, n_paths, err, ctx->sms,
-                                                           ctx->stream, jobs));
+                                                           ctx->stream, jobs, wide));
             else
                 LAUNCH(MCEV_K_EXTEND, launch_extend(ctx->dsc, fr.dev, P.t_min, w, cur ^ 1, n_paths, err, ctx->sms,
-                                                    ctx->stream, jobs));
+                                                    ctx->stream, jobs, wide));
 #else
             if (nee)
                 LAUNCH(MCEV_K_SHADOW, launch_shadow(ctx->dsc, fr.dev, P, w, cur, n_paths, err, ctx->sms, ctx->stream,
-                                                    jobs));
+                                                    jobs, wide));
             LAUNCH(MCEV_K_EXTEND, launch_extend(ctx->dsc, fr.dev, P.t_min, w, cur ^ 1, n_paths, err, ctx->sms,
-                                                ctx->stream, jobs));
+                                                ctx->stream, jobs, wide));
 #endif
         }
         cur ^= 1;
@@ -983,7 +1020,7 @@ void mcev_destroy(mcev_ctx* ctx) {
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
-    DevBuf* bufs[] = {&ctx->d_nodes, &ctx->d_tris, &ctx->d_uv, &ctx->d_mats, &ctx->d_env, &ctx->d_marg, &ctx->d_cond,
+    DevBuf* bufs[] = {&ctx->d_nodes, &ctx->d_wnodes, &ctx->d_tris, &ctx->d_uv, &ctx->d_mats, &ctx->d_env, &ctx->d_marg, &ctx->d_cond,
                       &ctx->d_tpdf, &ctx->frames[0].buf, &ctx->frames[1].buf, &ctx->d_wave, &ctx->d_counters,
                       &ctx->d_pix, &ctx->d_tcrit, &ctx->d_jobs, &ctx->d_bqueue, &ctx->d_quality, &ctx->d_gemit};
     for (DevBuf* b : bufs) dev_free(ctx, *b);
@@ -1149,15 +1186,28 @@ mcev_status mcev_set_params(mcev_ctx* ctx, const mcev_params* p) {
     if (!(p->eps > 0.0f) || !(p->t_min >= 0.0f) || p->max_depth < 0 || p->max_depth > 64 || p->spp_min < 2 ||
         p->variant < 0 || p->variant > 3 || p->se_mode < 0 || p->se_mode > 1 || p->wavefront < 0 ||
         p->batch_window < 0 || p->batch_window > 1024 ||
-        (p->wavefront > 0 && p->wavefront < 1024) || p->wavefront > ((int64_t)1 << 30))
+        (p->wavefront > 0 && p->wavefront < 1024) || p->wavefront > ((int64_t)1 << 30) ||
+        (p->bvh_width != 0 && p->bvh_width != 2 && p->bvh_width != 8))
         return fail(ctx, MCEV_ERR_ARG, "invalid render parameters");
     const bool reseed = p->seed != ctx->params.seed;
     const bool shape = p->eps != ctx->params.eps || p->t_min != ctx->params.t_min ||
                        p->max_depth != ctx->params.max_depth || p->nee != ctx->params.nee || p->mis != ctx->params.mis;
+    const int width = p->bvh_width ? p->bvh_width : MCEV_DEFAULT_BVH_WIDTH;
     ctx->params = *p;
     if (reseed || shape) {
         ctx->ref_valid = false;
         for (auto& f : ctx->frames) f.valid = false;
+    }
+    if (width != ctx->bvh_width) {
+        ctx->bvh_width = width;
+        if (ctx->have_scene) {
+            CU(cudaSetDevice(ctx->device));
+            const mcev_status st = build_blas(ctx);
+            if (st != MCEV_OK) {
+                ctx->have_scene = false;   // half-built: the scene must be uploaded again
+                return st;
+            }
+        }
     }
     return MCEV_OK;
 }
@@ -1321,6 +1371,8 @@ mcev_status mcev_render_events_batch(mcev_ctx* runner, const mcev_job* jobs, int
         if (!jobs[i].events_out) return fail(ctx, MCEV_ERR_ARG, "job %d: events_out is required", i);
         if (c->params.spp_min != spp_min || c->params.variant != variant || c->params.se_mode != se_mode)
             return fail(ctx, MCEV_ERR_ARG, "job %d: spp_min, variant and se_mode must match across jobs", i);
+        if (c->bvh_width != j0c->bvh_width)
+            return fail(ctx, MCEV_ERR_ARG, "job %d: every job's BVH must use the same node layout", i);
         for (int k = 0; k < i; ++k)
             if (jobs[k].ctx == c) return fail(ctx, MCEV_ERR_ARG, "jobs %d and %d share a context", k, i);
     }
@@ -1340,6 +1392,7 @@ mcev_status mcev_render_events_batch(mcev_ctx* runner, const mcev_job* jobs, int
     ST(dev_alloc(ctx, ctx->d_bqueue, 2 * sizeof(int32_t) * (size_t)total));
     ST(dev_alloc(ctx, ctx->d_jobs, sizeof(Job) * (size_t)n_jobs));
     BatchRun B;
+    B.wide = j0c->bvh_width == 8;
     B.d_jobs = (const Job*)ctx->d_jobs.ptr;
     B.queue[0] = (int32_t*)ctx->d_bqueue.ptr;
     B.queue[1] = B.queue[0] + total;

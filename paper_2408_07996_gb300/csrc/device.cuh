@@ -349,7 +349,7 @@ __device__ __forceinline__ bool better_hit(float t, int inst, int prim, const Hi
 // static geometry whose triangles carry their own instance id (v2.w).
 __device__ __forceinline__ bool step_closest(const DevScene& sc, int rec, int inst, const WRay& r, float tmin,
                                              Hit& h, int* stack, int base, int& sp, int& node, int* err,
-                                             int2& work) {
+                                             int3& work) {
     const Node n = load_node(sc.nodes, node);
     work.x += 1;
     float tl, tr;
@@ -395,7 +395,7 @@ __device__ __forceinline__ bool step_closest(const DevScene& sc, int rec, int in
 }
 
 __device__ __forceinline__ void blas_closest(const DevScene& sc, int root, int rec, int inst, const WRay& r,
-                                             float tmin, Hit& h, int* stack, int base, int* err, int2& work) {
+                                             float tmin, Hit& h, int* stack, int base, int* err, int3& work) {
     int sp = base;
     int node = root;
     while (step_closest(sc, rec, inst, r, tmin, h, stack, base, sp, node, err, work)) {
@@ -405,7 +405,7 @@ __device__ __forceinline__ void blas_closest(const DevScene& sc, int root, int r
 // One node of an any-hit BLAS traversal.  Returns 0 to continue, 1 when
 // finished without a hit, 2 when an occluder was found.
 __device__ __forceinline__ int step_any(const DevScene& sc, const WRay& r, float tmin, float tmax, int* stack,
-                                        int base, int& sp, int& node, int* err, int2& work) {
+                                        int base, int& sp, int& node, int* err, int3& work) {
     const Node n = load_node(sc.nodes, node);
     work.x += 1;
     float tl, tr;
@@ -451,13 +451,144 @@ __device__ __forceinline__ int step_any(const DevScene& sc, const WRay& r, float
 }
 
 __device__ __forceinline__ bool blas_any(const DevScene& sc, int root, const WRay& r, float tmin, float tmax,
-                                         int* stack, int base, int* err, int2& work) {
+                                         int* stack, int base, int* err, int3& work) {
     int sp = base;
     int node = root;
     while (true) {
         const int s = step_any(sc, r, tmin, tmax, stack, base, sp, node, err, work);
         if (s) return s == 2;
     }
+}
+
+// ------------------------------------------------------------------ compressed 8-wide BLAS
+// Traversal of the Node8 layout (layout.h).  A "node group" is a 64-bit word
+// pair (child_base, bits): bits 24..31 mark the internal children of one node
+// still to visit, indexed by visit key = slot ^ ox (ox: bit a set when the
+// ray's direction component a is >= 0, so children on the -a side come first),
+// bits 0..7 hold that node's imask, so slot s's node is
+// child_base + popc(imask below s).
+#define MCEV_WSTACK MCEV_WSTACK_HOST
+
+// 1 + q * 2^-15 for the byte q of `w` at position b (a float whose mantissa
+// holds q: 0x3F80_qq_00), built by one byte permute
+__device__ __forceinline__ float qplane(uint32_t w, int b) {
+    return __uint_as_float(__byte_perm(w, 0x3F800000u, 0x7604u | ((uint32_t)b << 4)));
+}
+
+// bit s of x moved to bit s ^ ox (x: 8 bits)
+__device__ __forceinline__ uint32_t xor_permute8(uint32_t x, uint32_t ox) {
+    x = (ox & 1u) ? (((x & 0x55u) << 1) | ((x >> 1) & 0x55u)) : x;
+    x = (ox & 2u) ? (((x & 0x33u) << 2) | ((x >> 2) & 0x33u)) : x;
+    x = (ox & 4u) ? (((x & 0x0Fu) << 4) | ((x >> 4) & 0x0Fu)) : x;
+    return x;
+}
+
+// bit s of x (8 bits) copied to bits 3s, 3s+1, 3s+2
+__device__ __forceinline__ uint32_t spread3(uint32_t x) {
+    x = (x | (x << 8)) & 0x00F00Fu;
+    x = (x | (x << 4)) & 0x0C30C3u;
+    x = (x | (x << 2)) & 0x249249u;
+    return x * 7u;
+}
+
+// Tests the up to eight child boxes of wide node `idx` against the ray over
+// [tmin, tmax].  Returns the 8-bit mask of hit slots and the node's child and
+// triangle bases, imask and triangle mask.  A plane at q grid steps is
+// p + q * 2^k; with f = 1 + q 2^-15 its ray parameter is f * A + B,
+// A = 2^(k+15) / d, B = (p - o) / d - A: one FMA per plane, A exact, the
+// other roundings far inside the 1/16-step margin the builder leaves around
+// every child box.
+__device__ __forceinline__ uint32_t wide_node_hits(const uint4* __restrict__ wn, uint32_t idx, const WRay& r,
+                                                   uint32_t ox, float tmin, float tmax, uint32_t& child_base,
+                                                   uint32_t& tri_base, uint32_t& imask, uint32_t& trimask,
+                                                   int& nvalid) {
+    const uint4* np = wn + 5 * (size_t)idx;
+    const uint4 v0 = __ldg(np), v1 = __ldg(np + 1), v2 = __ldg(np + 2), v3 = __ldg(np + 3), v4 = __ldg(np + 4);
+    const float Ax = __uint_as_float(((v0.w & 0xFFu) + 15u) << 23) * r.idir.x;
+    const float Ay = __uint_as_float((((v0.w >> 8) & 0xFFu) + 15u) << 23) * r.idir.y;
+    const float Az = __uint_as_float((((v0.w >> 16) & 0xFFu) + 15u) << 23) * r.idir.z;
+    const float Bx = fmaf(__uint_as_float(v0.x) - r.o.x, r.idir.x, -Ax);
+    const float By = fmaf(__uint_as_float(v0.y) - r.o.y, r.idir.y, -Ay);
+    const float Bz = fmaf(__uint_as_float(v0.z) - r.o.z, r.idir.z, -Az);
+    child_base = v1.x;
+    tri_base = v1.y & 0x1FFFFFFFu;
+    nvalid = (int)(v1.y >> 29) + 1;
+    trimask = v1.z;
+    imask = v0.w >> 24;
+    // near and far plane words per axis: the low planes are near for d >= 0
+    const bool sx = (ox & 1u) != 0, sy = (ox & 2u) != 0, sz = (ox & 4u) != 0;
+    const uint32_t nx[2] = {sx ? v2.x : v3.z, sx ? v2.y : v3.w}, fx[2] = {sx ? v3.z : v2.x, sx ? v3.w : v2.y};
+    const uint32_t ny[2] = {sy ? v2.z : v4.x, sy ? v2.w : v4.y}, fy[2] = {sy ? v4.x : v2.z, sy ? v4.y : v2.w};
+    const uint32_t nz[2] = {sz ? v3.x : v4.z, sz ? v3.y : v4.w}, fz[2] = {sz ? v4.z : v3.x, sz ? v4.w : v3.y};
+    uint32_t hit8 = 0;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const float tnx = fmaf(qplane(nx[h], b), Ax, Bx), tfx = fmaf(qplane(fx[h], b), Ax, Bx);
+            const float tny = fmaf(qplane(ny[h], b), Ay, By), tfy = fmaf(qplane(fy[h], b), Ay, By);
+            const float tnz = fmaf(qplane(nz[h], b), Az, Bz), tfz = fmaf(qplane(fz[h], b), Az, Bz);
+            const float tn = max3f(tnx, tny, fmaxf(tnz, tmin));
+            const float tf = min3f(tfx, tfy, fminf(tfz, tmax));
+            if (tn <= tf) hit8 |= 1u << (4 * h + b);
+        }
+    }
+    return hit8;
+}
+
+// Closest hit (kAny = false; updates h) or any hit in (tmin, tmax] (kAny =
+// true; returns true at the first occluder) of an object-space ray in the
+// wide BLAS rooted at `root`.  work: (node fetches, triangle tests, box tests).
+template <bool kAny>
+__device__ __forceinline__ bool blas_wide(const DevScene& sc, uint32_t root, int rec, int inst, const WRay& r,
+                                          float tmin, float tmax, Hit& h, uint2* stack, int* err, int3& work) {
+    const uint32_t ox = (r.idir.x >= 0.0f ? 1u : 0u) | (r.idir.y >= 0.0f ? 2u : 0u) | (r.idir.z >= 0.0f ? 4u : 0u);
+    // the root as the only (internal, slot 0) child of a virtual parent
+    uint2 g = make_uint2(root, (1u << (24 + ox)) | 1u);
+    int sp = 0;
+    while (true) {
+        uint32_t tb = 0, tbits = 0, tmask = 0;
+        if (g.y & 0xFF000000u) {
+            const uint32_t key = __ffs(g.y >> 24) - 1;
+            g.y &= ~(1u << (24 + key));
+            const uint32_t slot = key ^ ox;
+            const uint32_t child = g.x + __popc(g.y & ((1u << slot) - 1u) & 0xFFu);
+            if (g.y & 0xFF000000u) {
+                if (sp < MCEV_WSTACK) stack[sp++] = g;
+                else *err = 1;
+            }
+            uint32_t cb, im;
+            int nv;
+            const uint32_t hit8 =
+                wide_node_hits(sc.wnodes, child, r, ox, tmin, kAny ? tmax : h.t, cb, tb, im, tmask, nv);
+            work.x += 1;
+            work.z += nv;
+            g = make_uint2(cb, (xor_permute8(hit8 & im, ox) << 24) | im);
+            tbits = spread3(hit8 & ~im) & tmask;
+        }
+        while (tbits) {
+            const uint32_t bit = (uint32_t)(__ffs(tbits) - 1);
+            tbits &= tbits - 1;
+            const uint32_t ti = tb + __popc(tmask & ((1u << bit) - 1u));
+            const float4* tp = sc.tris + 3 * ti;
+            const float4 p0 = __ldg(tp), p1 = __ldg(tp + 1), p2 = __ldg(tp + 2);
+            work.y += 1;
+            const float t = tri_hit(r, p0, p1, p2, tmin, kAny ? tmax : h.t);
+            if (kAny) {
+                if (t >= 0.0f) return true;
+            } else {
+                const int oi = inst >= 0 ? inst : __float_as_int(p2.w);
+                if (t >= 0.0f && better_hit(t, oi, __float_as_int(p0.w), h)) {
+                    h.t = t; h.inst = oi; h.tri = (int)ti; h.prim = __float_as_int(p0.w); h.rec = rec;
+                }
+            }
+        }
+        if (!(g.y & 0xFF000000u)) {
+            if (sp == 0) break;
+            g = stack[--sp];
+        }
+    }
+    return false;
 }
 
 // instance record: rows M0..M2, Minv0..Minv2, (root, override, instance id, 0)
@@ -470,9 +601,38 @@ __device__ __forceinline__ WRay object_ray(const DevFrame& fr, int rec, f3 o, f3
     return make_wray(xf_point(i0, i1, i2, o), xf_vec(i0, i1, i2, d));
 }
 
-// world-space closest hit over the two-level hierarchy
+// BLAS traversal of either layout; `stack`/`base` are the two-wide stack,
+// `wstack` the wide one.  work.z (box tests) is kept for the wide layout only:
+// a two-wide node fetch always tests two boxes.
+template <bool kWide>
+__device__ __forceinline__ void blas_closest_any_layout(const DevScene& sc, int root, int rec, int inst, const WRay& r,
+                                                        float tmin, Hit& h, int* stack, int base, uint2* wstack,
+                                                        int* err, int3& work) {
+    if (kWide) {
+        blas_wide<false>(sc, (uint32_t)root, rec, inst, r, tmin, 0.0f, h, wstack, err, work);
+    } else {
+        blas_closest(sc, root, rec, inst, r, tmin, h, stack, base, err, work);
+    }
+}
+
+template <bool kWide>
+__device__ __forceinline__ bool blas_any_layout(const DevScene& sc, int root, const WRay& r, float tmin, float tmax,
+                                                int* stack, int base, uint2* wstack, int* err, int3& work) {
+    if (kWide) {
+        Hit dummy;
+        return blas_wide<true>(sc, (uint32_t)root, 0, 0, r, tmin, tmax, dummy, wstack, err, work);
+    }
+    return blas_any(sc, root, r, tmin, tmax, stack, base, err, work);
+}
+
+#define MCEV_DECLARE_WSTACK(name) uint2 name[kWide ? MCEV_WSTACK : 1]
+
+// world-space closest hit over the two-level hierarchy (the TLAS is two-wide;
+// BLAS in the scene's layout).  work: (node fetches, triangle tests, box
+// tests of the wide layout)
+template <bool kWide>
 __device__ __forceinline__ Hit closest_hit(const DevScene& sc, const DevFrame& fr, f3 o, f3 d, float tmin, int* err,
-                                           int2& work) {
+                                           int3& work) {
     Hit h;
     h.t = __int_as_float(0x7f800000);
     h.inst = -1;
@@ -480,11 +640,12 @@ __device__ __forceinline__ Hit closest_hit(const DevScene& sc, const DevFrame& f
     h.prim = -1;
     h.rec = -1;
     MCEV_DECLARE_STACK(stack);
+    MCEV_DECLARE_WSTACK(wstack);
     if (fr.n_inst == 0) return h;
     if (fr.tlas_is_leaf) {
         int root, oi;
         const WRay r = object_ray(fr, 0, o, d, root, oi);
-        blas_closest(sc, root, 0, oi, r, tmin, h, stack, 0, err, work);
+        blas_closest_any_layout<kWide>(sc, root, 0, oi, r, tmin, h, stack, 0, wstack, err, work);
         return h;
     }
     const WRay wr = make_wray(o, d);
@@ -493,6 +654,7 @@ __device__ __forceinline__ Hit closest_hit(const DevScene& sc, const DevFrame& f
     while (true) {
         const Node n = load_node(fr.tlas, node);
         work.x += 1;
+        if (kWide) work.z += 2;
         float tl, tr;
         const int m = node_hits(wr, n, tmin, h.t, tl, tr);
         for (int side = 0; side < 2; ++side) {
@@ -503,7 +665,7 @@ __device__ __forceinline__ Hit closest_hit(const DevScene& sc, const DevFrame& f
                     const int rec = ~child + i;
                     int root, oi;
                     const WRay r = object_ray(fr, rec, o, d, root, oi);
-                    blas_closest(sc, root, rec, oi, r, tmin, h, stack, sp, err, work);
+                    blas_closest_any_layout<kWide>(sc, root, rec, oi, r, tmin, h, stack, sp, wstack, err, work);
                 }
             }
         }
@@ -530,14 +692,16 @@ __device__ __forceinline__ Hit closest_hit(const DevScene& sc, const DevFrame& f
     return h;
 }
 
+template <bool kWide>
 __device__ __forceinline__ bool occluded(const DevScene& sc, const DevFrame& fr, f3 o, f3 d, float tmin, float tmax,
-                                         int* err, int2& work) {
+                                         int* err, int3& work) {
     MCEV_DECLARE_STACK(stack);
+    MCEV_DECLARE_WSTACK(wstack);
     if (fr.n_inst == 0) return false;
     if (fr.tlas_is_leaf) {
         int root, oi;
         const WRay r = object_ray(fr, 0, o, d, root, oi);
-        return blas_any(sc, root, r, tmin, tmax, stack, 0, err, work);
+        return blas_any_layout<kWide>(sc, root, r, tmin, tmax, stack, 0, wstack, err, work);
     }
     const WRay wr = make_wray(o, d);
     int sp = 0;
@@ -545,6 +709,7 @@ __device__ __forceinline__ bool occluded(const DevScene& sc, const DevFrame& fr,
     while (true) {
         const Node n = load_node(fr.tlas, node);
         work.x += 1;
+        if (kWide) work.z += 2;
         float tl, tr;
         const int m = node_hits(wr, n, tmin, tmax, tl, tr);
         for (int side = 0; side < 2; ++side) {
@@ -555,7 +720,7 @@ __device__ __forceinline__ bool occluded(const DevScene& sc, const DevFrame& fr,
                     const int rec = ~child + i;
                     int root, oi;
                     const WRay r = object_ray(fr, rec, o, d, root, oi);
-                    if (blas_any(sc, root, r, tmin, tmax, stack, sp, err, work)) return true;
+                    if (blas_any_layout<kWide>(sc, root, r, tmin, tmax, stack, sp, wstack, err, work)) return true;
                 }
             }
         }

@@ -29,11 +29,12 @@ namespace mcev {
 #ifndef MCEV_TRAV_MINB
 #define MCEV_TRAV_MINB 8
 #endif
-#if MCEV_TRAV_MINB > 0
-#define MCEV_TRAV_BOUNDS __launch_bounds__(MCEV_TRAV_BLOCK, MCEV_TRAV_MINB)
-#else
-#define MCEV_TRAV_BOUNDS __launch_bounds__(MCEV_TRAV_BLOCK)
+// The wide-node traversal keeps a whole node (five 16-byte words) and its
+// eight child tests in flight: it gets its own cap.
+#ifndef MCEV_WIDE_MINB
+#define MCEV_WIDE_MINB 8
 #endif
+#define MCEV_TRAV_BOUNDS __launch_bounds__(MCEV_TRAV_BLOCK, kWide ? MCEV_WIDE_MINB : MCEV_TRAV_MINB)
 
 static constexpr uint32_t NO_FLAGS = 0xFFFFFFFFu;
 
@@ -93,15 +94,17 @@ __global__ void __launch_bounds__(256) k_raygen(DevFrame fr, DevParams P, Wave w
 // traversal work counters: 64-bit (nodes, tris) pairs after the int32
 // counters, and the ray/box tests (two per node fetch of the two-wide BVH)
 enum { WORK_CLOSEST = 0, WORK_SHADOW = 1 };
-__device__ __forceinline__ void add_work(const Wave& w, int which, int2 work) {
+template <bool kWide>
+__device__ __forceinline__ void add_work(const Wave& w, int which, int3 work) {
     const unsigned m = __activemask();
     const int nodes = __reduce_add_sync(m, work.x);
     const int tris = __reduce_add_sync(m, work.y);
+    const int boxes = kWide ? __reduce_add_sync(m, work.z) : 2 * nodes;
     if ((threadIdx.x & 31) == (__ffs(m) - 1)) {
         unsigned long long* c = reinterpret_cast<unsigned long long*>(w.counters + 32);
         atomicAdd(c + 2 * which, (unsigned long long)nodes);
         atomicAdd(c + 2 * which + 1, (unsigned long long)tris);
-        atomicAdd(c + 7 + which, 2ull * (unsigned long long)nodes);
+        atomicAdd(c + 7 + which, (unsigned long long)boxes);
     }
 }
 
@@ -109,7 +112,7 @@ __device__ __forceinline__ void add_work(const Wave& w, int which, int2 work) {
 // Closest hits of the rays of queue `cur`, indices first, first + stride, ...
 // The first thread also clears the queue and shadow counters shade(cur) will
 // append to.
-template <bool kBatch>
+template <bool kBatch, bool kWide>
 __device__ __forceinline__ void extend_rays(const DevScene& sc, const DevFrame& fr, float t_min, const Wave& w,
                                             int cur, int32_t* err, const Job* __restrict__ jobs, int64_t first,
                                             int64_t stride) {
@@ -120,7 +123,7 @@ __device__ __forceinline__ void extend_rays(const DevScene& sc, const DevFrame& 
         atomicAdd(reinterpret_cast<unsigned long long*>(w.counters + 32) + 4, (unsigned long long)n);
     }
     int e = 0;
-    int2 work = make_int2(0, 0);
+    int3 work = make_int3(0, 0, 0);
     for (int64_t i = first; i < n; i += stride) {
         const float4 o = w.ray_o[cur][i];
         const float4 d = w.ray_d[cur][i];
@@ -128,18 +131,18 @@ __device__ __forceinline__ void extend_rays(const DevScene& sc, const DevFrame& 
         const DevScene& S = kBatch ? jobs[job].sc : sc;
         const DevFrame& F = kBatch ? jobs[job].fr : fr;
         const float tmin = kBatch ? jobs[job].P.t_min : t_min;
-        const Hit h = closest_hit(S, F, xyz(o), xyz(d), tmin, &e, work);
+        const Hit h = closest_hit<kWide>(S, F, xyz(o), xyz(d), tmin, &e, work);
         w.hit[i] = make_float4(h.t, __int_as_float(h.inst), __int_as_float(h.tri), __int_as_float(h.rec));
     }
     if (e) atomicOr(err, 1);
-    add_work(w, WORK_CLOSEST, work);
+    add_work<kWide>(w, WORK_CLOSEST, work);
 }
 
-template <bool kBatch>
+template <bool kBatch, bool kWide>
 __global__ void MCEV_TRAV_BOUNDS k_extend(DevScene sc, DevFrame fr, float t_min, Wave w, int cur, int32_t* err,
                                           const Job* __restrict__ jobs) {
-    extend_rays<kBatch>(sc, fr, t_min, w, cur, err, jobs, blockIdx.x * (int64_t)blockDim.x + threadIdx.x,
-                        (int64_t)gridDim.x * blockDim.x);
+    extend_rays<kBatch, kWide>(sc, fr, t_min, w, cur, err, jobs, blockIdx.x * (int64_t)blockDim.x + threadIdx.x,
+                               (int64_t)gridDim.x * blockDim.x);
 }
 
 // ------------------------------------------------------------------ shade + NEE + BSDF sampling
@@ -360,14 +363,14 @@ __global__ void MCEV_SHADE_BOUNDS k_shade(DevScene sc, DevFrame fr, DevParams P,
 
 // ------------------------------------------------------------------ shadow rays
 // Shadow rays appended by shade(cur), indices first, first + stride, ...
-template <bool kBatch>
+template <bool kBatch, bool kWide>
 __device__ __forceinline__ void shadow_rays(const DevScene& sc, const DevFrame& fr, const DevParams& P,
                                             const Wave& w, int cur, int32_t* err, const Job* __restrict__ jobs,
                                             int64_t first, int64_t stride) {
     const int32_t n = *(volatile int32_t*)(w.counters + sh_slot(cur));
     if (first == 0) atomicAdd(reinterpret_cast<unsigned long long*>(w.counters + 32) + 5, (unsigned long long)n);
     int e = 0;
-    int2 work = make_int2(0, 0);
+    int3 work = make_int3(0, 0, 0);
     for (int64_t i = first; i < n; i += stride) {
         const float4 o = w.sh_o[i];
         const float4 d = w.sh_d[i];
@@ -376,7 +379,7 @@ __device__ __forceinline__ void shadow_rays(const DevScene& sc, const DevFrame& 
         const DevScene& S = kBatch ? jobs[job].sc : sc;
         const DevFrame& F = kBatch ? jobs[job].fr : fr;
         const DevParams& Q = kBatch ? jobs[job].P : P;
-        if (!occluded(S, F, xyz(o), xyz(d), Q.t_min, d.w, &e, work)) {
+        if (!occluded<kWide>(S, F, xyz(o), xyz(d), Q.t_min, d.w, &e, work)) {
             w.L[p] += w.sh_c[i];
             if (Q.want_sig) w.pflags[p] |= 4u;
             if (Q.adjoint && Q.grad_emit && w.sh_m[i] >= 0)
@@ -384,30 +387,30 @@ __device__ __forceinline__ void shadow_rays(const DevScene& sc, const DevFrame& 
         }
     }
     if (e) atomicOr(err, 1);
-    add_work(w, WORK_SHADOW, work);
+    add_work<kWide>(w, WORK_SHADOW, work);
 }
 
-template <bool kBatch>
+template <bool kBatch, bool kWide>
 __global__ void MCEV_TRAV_BOUNDS k_shadow(DevScene sc, DevFrame fr, DevParams P, Wave w, int cur, int32_t* err,
                                           const Job* __restrict__ jobs) {
-    shadow_rays<kBatch>(sc, fr, P, w, cur, err, jobs, blockIdx.x * (int64_t)blockDim.x + threadIdx.x,
-                        (int64_t)gridDim.x * blockDim.x);
+    shadow_rays<kBatch, kWide>(sc, fr, P, w, cur, err, jobs, blockIdx.x * (int64_t)blockDim.x + threadIdx.x,
+                               (int64_t)gridDim.x * blockDim.x);
 }
 
 // One launch for the shadow rays of bounce d (appended by shade with queue
 // `cur`) and the closest hits of bounce d + 1 (queue 1 - cur): the first
 // `g_ext` blocks extend, the rest trace shadow rays.  Two independent traversal
 // workloads in one grid keep the SMs busy while the other's longest rays finish.
-template <bool kBatch>
+template <bool kBatch, bool kWide>
 __global__ void MCEV_TRAV_BOUNDS k_shadow_extend(DevScene sc, DevFrame fr, DevParams P, Wave w, int cur,
                                                  int32_t g_ext, int32_t* err, const Job* __restrict__ jobs) {
     if ((int32_t)blockIdx.x < g_ext)
-        extend_rays<kBatch>(sc, fr, P.t_min, w, 1 - cur, err, jobs, blockIdx.x * (int64_t)blockDim.x + threadIdx.x,
-                            (int64_t)g_ext * blockDim.x);
+        extend_rays<kBatch, kWide>(sc, fr, P.t_min, w, 1 - cur, err, jobs,
+                                   blockIdx.x * (int64_t)blockDim.x + threadIdx.x, (int64_t)g_ext * blockDim.x);
     else
-        shadow_rays<kBatch>(sc, fr, P, w, cur, err, jobs,
-                            (blockIdx.x - g_ext) * (int64_t)blockDim.x + threadIdx.x,
-                            (int64_t)(gridDim.x - g_ext) * blockDim.x);
+        shadow_rays<kBatch, kWide>(sc, fr, P, w, cur, err, jobs,
+                                   (blockIdx.x - g_ext) * (int64_t)blockDim.x + threadIdx.x,
+                                   (int64_t)(gridDim.x - g_ext) * blockDim.x);
 }
 
 // ------------------------------------------------------------------ per-pixel statistics + test + requeue + events
@@ -623,14 +626,18 @@ cudaError_t launch_raygen(const DevFrame& fr, const DevParams& P, const Wave& w,
     return cudaGetLastError();
 }
 
+// traversal launches: kBatch x kWide instantiations picked at run time
+#define MCEV_TRAV_DISPATCH(kernel, grid, ...)                                                              \
+    do {                                                                                                   \
+        if (jobs && wide) kernel<true, true><<<grid, MCEV_TRAV_BLOCK, 0, st>>>(__VA_ARGS__, jobs);          \
+        else if (jobs) kernel<true, false><<<grid, MCEV_TRAV_BLOCK, 0, st>>>(__VA_ARGS__, jobs);            \
+        else if (wide) kernel<false, true><<<grid, MCEV_TRAV_BLOCK, 0, st>>>(__VA_ARGS__, nullptr);         \
+        else kernel<false, false><<<grid, MCEV_TRAV_BLOCK, 0, st>>>(__VA_ARGS__, nullptr);                  \
+    } while (0)
+
 cudaError_t launch_extend(const DevScene& sc, const DevFrame& fr, float t_min, const Wave& w, int cur, int64_t max_n,
-                          int32_t* err, int sms, cudaStream_t st, const Job* jobs) {
-    if (jobs)
-        k_extend<true><<<grid_for(max_n, MCEV_TRAV_BLOCK, sms, 16), MCEV_TRAV_BLOCK, 0, st>>>(sc, fr, t_min, w, cur,
-                                                                                              err, jobs);
-    else
-        k_extend<false><<<grid_for(max_n, MCEV_TRAV_BLOCK, sms, 16), MCEV_TRAV_BLOCK, 0, st>>>(sc, fr, t_min, w, cur,
-                                                                                               err, nullptr);
+                          int32_t* err, int sms, cudaStream_t st, const Job* jobs, bool wide) {
+    MCEV_TRAV_DISPATCH(k_extend, grid_for(max_n, MCEV_TRAV_BLOCK, sms, 16), sc, fr, t_min, w, cur, err);
     return cudaGetLastError();
 }
 
@@ -644,23 +651,15 @@ cudaError_t launch_shade(const DevScene& sc, const DevFrame& fr, const DevParams
 }
 
 cudaError_t launch_shadow(const DevScene& sc, const DevFrame& fr, const DevParams& P, const Wave& w, int cur,
-                          int64_t max_n, int32_t* err, int sms, cudaStream_t st, const Job* jobs) {
-    if (jobs)
-        k_shadow<true><<<grid_for(max_n, MCEV_TRAV_BLOCK, sms, 16), MCEV_TRAV_BLOCK, 0, st>>>(sc, fr, P, w, cur, err,
-                                                                                              jobs);
-    else
-        k_shadow<false><<<grid_for(max_n, MCEV_TRAV_BLOCK, sms, 16), MCEV_TRAV_BLOCK, 0, st>>>(sc, fr, P, w, cur, err,
-                                                                                               nullptr);
+                          int64_t max_n, int32_t* err, int sms, cudaStream_t st, const Job* jobs, bool wide) {
+    MCEV_TRAV_DISPATCH(k_shadow, grid_for(max_n, MCEV_TRAV_BLOCK, sms, 16), sc, fr, P, w, cur, err);
     return cudaGetLastError();
 }
 
 cudaError_t launch_shadow_extend(const DevScene& sc, const DevFrame& fr, const DevParams& P, const Wave& w, int cur,
-                                 int64_t max_n, int32_t* err, int sms, cudaStream_t st, const Job* jobs) {
+                                 int64_t max_n, int32_t* err, int sms, cudaStream_t st, const Job* jobs, bool wide) {
     const int g = grid_for(max_n, MCEV_TRAV_BLOCK, sms, 16);
-    if (jobs)
-        k_shadow_extend<true><<<2 * g, MCEV_TRAV_BLOCK, 0, st>>>(sc, fr, P, w, cur, g, err, jobs);
-    else
-        k_shadow_extend<false><<<2 * g, MCEV_TRAV_BLOCK, 0, st>>>(sc, fr, P, w, cur, g, err, nullptr);
+    MCEV_TRAV_DISPATCH(k_shadow_extend, 2 * g, sc, fr, P, w, cur, g, err);
     return cudaGetLastError();
 }
 

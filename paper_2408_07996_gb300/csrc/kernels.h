@@ -31,15 +31,16 @@ struct StatsArgs {
 cudaError_t launch_raygen(const DevFrame& fr, const DevParams& P, const Wave& w, const int32_t* queue, int64_t j0,
                           int32_t spp_r, int64_t k_base, int64_t n_paths, int cur, int sms, cudaStream_t st,
                           const Job* jobs);
+// `wide`: the scenes' BLAS use the compressed 8-wide layout (Node8)
 cudaError_t launch_extend(const DevScene& sc, const DevFrame& fr, float t_min, const Wave& w, int cur, int64_t max_n,
-                          int32_t* err, int sms, cudaStream_t st, const Job* jobs);
+                          int32_t* err, int sms, cudaStream_t st, const Job* jobs, bool wide);
 cudaError_t launch_shade(const DevScene& sc, const DevFrame& fr, const DevParams& P, const Wave& w, int cur,
                          int64_t max_n, int sms, cudaStream_t st, const Job* jobs);
 cudaError_t launch_shadow(const DevScene& sc, const DevFrame& fr, const DevParams& P, const Wave& w, int cur,
-                          int64_t max_n, int32_t* err, int sms, cudaStream_t st, const Job* jobs);
+                          int64_t max_n, int32_t* err, int sms, cudaStream_t st, const Job* jobs, bool wide);
 // shadow rays of the bounce with queue `cur` and closest hits of queue 1 - cur, in one launch
 cudaError_t launch_shadow_extend(const DevScene& sc, const DevFrame& fr, const DevParams& P, const Wave& w, int cur,
-                                 int64_t max_n, int32_t* err, int sms, cudaStream_t st, const Job* jobs);
+                                 int64_t max_n, int32_t* err, int sms, cudaStream_t st, const Job* jobs, bool wide);
 cudaError_t launch_stats(const Wave& w, const StatsArgs& A, const int32_t* queue, int64_t j0, int64_t n_pix,
                          int32_t* next_queue, int sms, cudaStream_t st, const Job* jobs);
 // out[i] += (float)acc[i] for i < n (the adjoint's FP64 emission accumulator)

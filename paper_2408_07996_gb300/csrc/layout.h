@@ -37,6 +37,9 @@
 #define MCEV_STACK_HOST 96
 #endif
 
+// Wide-BVH traversal stack per thread: node groups (one per wide level).
+#define MCEV_WSTACK_HOST 32
+
 namespace mcev {
 
 struct Node {
@@ -45,23 +48,26 @@ struct Node {
 };
 
 // Compressed 8-wide node (80 B, five 16-byte words): child boxes on a grid of
-// step 2^(e_a - 127) per axis a anchored at (px, py, pz); child slot i spans
-// [p + qlo[i] * step, p + qhi[i] * step] per axis (empty slots: qlo > qhi).
-//   e_imask : e_x | e_y << 8 | e_z << 16 | imask << 24  (imask bit i: slot i
+// step 2^(e_a - 127) per axis a anchored at (px, py, pz); child slot s spans
+// [p + qlo[s] * step, p + qhi[s] * step] per axis (empty slots: qlo > qhi),
+// every plane at least 1/16 step outside the child's exact box.
+//   e_imask : e_x | e_y << 8 | e_z << 16 | imask << 24  (imask bit s: slot s
 //             is an internal node)
 //   child_base: first child node; internal children are stored contiguously
-//             in slot order, so slot i's node is child_base + popc(imask below i)
-//   tri_base : bits 0..28 first triangle of the leaf children (contiguous);
-//             bits 29..31 number of non-empty slots - 1
-//   meta[i]  : internal: 0x20 | (24 + i); leaf: (2^count - 1) << 5 | offset of
-//             its first triangle from tri_base (count 1..3, offsets < 24);
-//             empty: 0.  (meta >> 5) << (meta & 31) is the slot's bit in a
-//             hit mask whose bits 24..31 are internal children, 0..23 triangles.
+//             in slot order, so slot s's node is child_base + popc(imask below s)
+//   tri_base : bits 0..28 first triangle of the leaf slots; bits 29..31 number
+//             of non-empty slots - 1
+//   trimask  : bit 3s + k set when slot s is a leaf of more than k triangles
+//             (1..3 per leaf); the triangles of the leaf slots are contiguous
+//             in slot order, so the one of bit b is tri_base + popc(trimask below b)
+//   slots are assigned by direction: slot bit a set = child on the -a side of
+//   the node centre, so a ray visits slot s in the order of s ^ ox, where ox
+//   has bit a set when the ray's direction component a is >= 0.
 struct Node8 {
     float px, py, pz;
     uint32_t e_imask;
     uint32_t child_base, tri_base;
-    uint32_t meta[2];
+    uint32_t trimask, pad;
     uint32_t qlo_x[2], qlo_y[2], qlo_z[2], qhi_x[2];
     uint32_t qhi_y[2], qhi_z[2];
 };

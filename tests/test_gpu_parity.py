@@ -67,10 +67,14 @@ def test_gpu_plane_and_empty_scene_exact():
 
 # ---------------------------------------------------------------- per-sample parity
 
+WIDTHS = [2, 8]      # BVH node layouts: two-wide, compressed 8-wide
+
+
+@pytest.mark.parametrize("width", WIDTHS)
 @pytest.mark.parametrize("t", [0.0, 1.0])
-def test_cornell_per_sample_parity(cornell, t):
+def test_cornell_per_sample_parity(cornell, t, width):
     w, osc = cornell
-    r = renderer_for(w, wavefront=5000)          # several chunks with a ragged tail
+    r = renderer_for(w, wavefront=5000, bvh_width=width)   # several chunks with a ragged tail
     pix = np.arange(0, 4096, 3)                  # 1366 pixels
     ps = per_sample(r, osc, O.params_of(w), t, pix, 5, 37, w.eps)
     s = summary(ps)
@@ -110,9 +114,10 @@ def _event_parity(r, osc, w, det, t0, t1, H, W, p):
                 dmean=dmean, ev=ev, n=n)
 
 
-def test_cornell_event_frame_parity(cornell):
+@pytest.mark.parametrize("width", WIDTHS)
+def test_cornell_event_frame_parity(cornell, width):
     w, osc = cornell
-    r = renderer_for(w)
+    r = renderer_for(w, bvh_width=width)
     res = _event_parity(r, osc, w, O.detect_of(w), 0.0, 1.0, w.height, w.width, O.params_of(w))
     print("cornell events: kept %.4f, topo-excluded %.4f, band-excluded %.4f, events %d/%d, mean n %.1f" % (
         res["keep"].mean(), 1 - res["topo_ok"].mean(), res["band"].mean(), (res["ev"] != 0).sum(),
@@ -250,11 +255,12 @@ def terrain():
     return w, O.OracleScene(w.scene)
 
 
+@pytest.mark.parametrize("width", WIDTHS)
 @pytest.mark.parametrize("k", [0, 5])
-def test_spheres_per_sample_parity(spheres, k):
+def test_spheres_per_sample_parity(spheres, k, width):
     # keyframe 5 has the spinning sphere turned; pixels span the whole image
     w, osc = spheres
-    r = renderer_for(w)
+    r = renderer_for(w, bvh_width=width)
     rng = np.random.default_rng(40 + k)
     pix = np.sort(rng.choice(w.width * w.height, size=1500, replace=False))
     ps = per_sample(r, osc, O.params_of(w), w.times[k], pix, 0, 24, w.eps)
@@ -267,9 +273,10 @@ def test_spheres_per_sample_parity(spheres, k):
     r.close()
 
 
-def test_terrain_per_sample_parity(terrain):
+@pytest.mark.parametrize("width", WIDTHS)
+def test_terrain_per_sample_parity(terrain, width):
     w, osc = terrain
-    r = renderer_for(w)
+    r = renderer_for(w, bvh_width=width)
     rng = np.random.default_rng(41)
     pix = np.sort(rng.choice(w.width * w.height, size=1200, replace=False))
     ps = per_sample(r, osc, O.params_of(w), w.times[3], pix, 100, 16, w.eps)
@@ -280,6 +287,37 @@ def test_terrain_per_sample_parity(terrain):
     full = ps["match"].all(axis=1)
     assert np.abs(ps["yg"].mean(1) - ps["yo"].mean(1))[full].max() < MEAN_TOL
     r.close()
+
+
+@pytest.mark.parametrize("name,k,n_pix,count", [("cornell64", 0, 4096, 16), ("spheres512", 5, 20000, 8),
+                                                  ("terrain720p", 3, 20000, 8)])
+def test_wide_bvh_matches_two_wide(name, k, n_pix, count):
+    """The compressed 8-wide BVH finds the same hits as the two-wide one: the
+    same triangle test decides every hit, so wherever a sample made the same
+    discrete decisions its radiance is bit-identical; decisions may differ
+    only where a box test is decided within rounding of the ray origin."""
+    w = sg.workload(name)
+    rng = np.random.default_rng(60 + k)
+    pix = torch.from_numpy(np.sort(rng.choice(w.width * w.height, size=min(n_pix, w.width * w.height),
+                                              replace=False)).astype(np.int32))
+    out = {}
+    for width in (2, 8):
+        r = renderer_for(w, bvh_width=width)
+        L, sig = r.trace_samples(w.times[k], pix, 0, count)
+        st = r.render_events(w.times[k], w.times[k + 1], w.C, w.alpha, w.spp_batch, w.spp_min)["stats"]
+        out[width] = (L.cpu().numpy(), sig.cpu().numpy(), st)
+        r.close()
+    same = out[2][1] == out[8][1]
+    print(name, "signature agreement %.6f" % same.mean(), "node fetches per ray: two-wide %.2f, wide %.2f" % (
+        (out[2][2]["nodes_closest"] + out[2][2]["nodes_shadow"]) / (out[2][2]["rays_closest"] + out[2][2]["rays_shadow"]),
+        (out[8][2]["nodes_closest"] + out[8][2]["nodes_shadow"]) / (out[8][2]["rays_closest"] + out[8][2]["rays_shadow"])))
+    assert 1 - same.mean() <= 1e-4
+    assert np.array_equal(out[2][0][same], out[8][0][same])
+    # traversal work counters of both layouts
+    s2, s8 = out[2][2], out[8][2]
+    assert s8["boxes_closest"] > 0 and s8["tris_closest"] > 0
+    assert s2["boxes_closest"] == 2 * s2["nodes_closest"]
+    assert s8["nodes_closest"] < s2["nodes_closest"]
 
 
 @pytest.mark.slow
