@@ -642,15 +642,35 @@ def main():
                   "frac": stats_bytes / (kms[4] / 1e3) / 1e9 / hbm_peak if kms[4] else None,
                   "bytes_per_frame": stats_bytes / K, "avg_launch_ms": kms[4] / max(1, kcnt[4])}
 
+    # the same K frames from the same reference with the library's default
+    # path: per-launch timing off, so the rounds run on the device as one
+    # CUDA graph per frame (no host round trip between rounds)
+    r.set_state(state0)
+    r.set_params(profile=0)
+    torch.cuda.synchronize()
+    barrier()
+    d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    d0.record()
+    dsteps = [dict(frame(k)["stats"]) for k in range(Wm, Wm + K)]
+    d1.record()
+    torch.cuda.synchronize()
+    dms = max_over_ranks(d0.elapsed_time(d1), dist, dev)
+    device_loop = {"frames_per_s": job_rate(K, dms / 1e3, world), "ms_per_frame": dms / K,
+                   "rounds_per_frame": sum(s["rounds"] for s in dsteps) / K,
+                   "gpu_launches": sum(s["kernel_launches"] for s in dsteps),
+                   "what": "same frames with per-launch timing off: each frame's rounds run as one CUDA graph "
+                           "(conditional loop sized on the device)"}
     line = {"metric": METRIC, "value": frames_per_s, "unit": "event frames/s", "n_gpus": world, "steps": K,
             "warmup": Wm, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": _config(w),
             "mpaths_per_s": mpaths, "paths_per_frame": paths / K,
             "mean_spp": paths / K / (H * Wd),
             "events_per_frame": sum(s["events_pos"] + s["events_neg"] for s in steps) / K,
-            "gpu_launches": launches, "roofline": roofline, "roofline_stats": roof_stats, "clocks": clk}
+            "gpu_launches": launches, "roofline": roofline, "roofline_stats": roof_stats, "clocks": clk,
+            "device_loop": device_loop}
 
     # uniform-spp comparator on the same GPU, same frame pair and reference
+    r.set_params(profile=1)
     if not args.no_uniform and rank == 0:
         kf = Wm + K
         st = r.get_state().clone()
@@ -705,6 +725,7 @@ def main():
     # the same reference, outputs copied to pinned host memory every step
     if not args.no_e2e:
         r.set_state(state0)
+        r.set_params(profile=0)      # the library's default path
         host = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in out.items()
                 if isinstance(v, torch.Tensor)}
         torch.cuda.synchronize()

@@ -39,7 +39,8 @@ typedef enum {
     MCEV_ERR_ARG = -1,      /* invalid argument (null, out of range, wrong size) */
     MCEV_ERR_CUDA = -2,     /* a CUDA runtime call failed; see mcev_last_error */
     MCEV_ERR_OOM = -3,      /* device or host allocation failed */
-    MCEV_ERR_TIMEOUT = -4,  /* reserved: a bounded device wait gave up */
+    MCEV_ERR_TIMEOUT = -4,  /* the device-resident round loop hit its bound (mcev_params.device_timeout_us,
+                               or more chunks than the sampling schedule can need); the frame is incomplete */
     MCEV_ERR_STATE = -5,    /* call out of order (e.g. render before scene upload) */
     MCEV_ERR_NUMERIC = -6   /* reserved for numeric failures surfaced as errors */
 } mcev_status;
@@ -119,6 +120,15 @@ typedef struct {
                            (compressed 8-wide nodes with 8-bit child boxes); 0 = library default.
                            Changing it rebuilds the BVHs of an uploaded scene.  Results are the
                            same up to rare FP32 box-culling decisions near a ray's origin. */
+    int32_t host_rounds;/* 0 (default): the rounds of a frame run on the device as one CUDA graph
+                           (a conditional loop: trace a chunk, merge and test, size the next chunk
+                           or round), with no host round trip until the frame is done; 1: the
+                           host drives the rounds, reading the number of undecided pixels back
+                           after each.  profile = 1 implies host-driven rounds (per-launch timing).
+                           Both give identical results. */
+    int32_t device_timeout_us; /* wall-clock bound of the device-resident loop in microseconds
+                           (0 = library default, 300 s); past it the loop stops after its current
+                           chunk and the call returns MCEV_ERR_TIMEOUT */
 } mcev_params;
 
 /* kernel classes reported in mcev_stats.  MCEV_K_EXTEND counts the traversal
@@ -154,45 +164,59 @@ typedef struct {
 } mcev_stats;
 
 /* Creates a context on CUDA device `device` for width x height images.
- * *out receives the context (NULL on failure).  Errors: ARG, CUDA, OOM. */
+ * *out receives the context (NULL on failure).  Errors: ARG, CUDA, OOM.
+ * No paper passage: infrastructure. */
 mcev_status mcev_create(mcev_ctx** out, int device, int32_t width, int32_t height);
 
-/* Frees every resource of the context (NULL is a no-op). */
+/* Frees every resource of the context (NULL is a no-op).
+ * No paper passage: infrastructure. */
 void mcev_destroy(mcev_ctx* ctx);
 
-/* Last error message of the context ("" when none); valid until the next call. */
+/* Last error message of the context ("" when none); valid until the next call.
+ * No paper passage: infrastructure. */
 const char* mcev_last_error(const mcev_ctx* ctx);
 
 /* Uses `stream` (a cudaStream_t, e.g. torch's current stream) for all later
- * GPU work of this context; NULL selects the legacy default stream. */
+ * GPU work of this context; NULL selects the legacy default stream.
+ * No paper passage: infrastructure. */
 mcev_status mcev_set_stream(mcev_ctx* ctx, void* stream);
 
 /* Routes the context's device allocations through alloc/free (e.g. a
  * framework's caching allocator).  alloc returns NULL on failure, which
  * the library reports as MCEV_ERR_OOM.  Must be called before
- * mcev_scene_upload; NULL restores cudaMalloc/cudaFree. */
+ * mcev_scene_upload; NULL restores cudaMalloc/cudaFree.
+ * No paper passage: infrastructure. */
 typedef void* (*mcev_alloc_fn)(size_t bytes, void* user);
 typedef void (*mcev_free_fn)(void* ptr, void* user);
 mcev_status mcev_set_allocator(mcev_ctx* ctx, mcev_alloc_fn alloc, mcev_free_fn free_fn, void* user);
 
 /* Copies the scene to the device (see mcev_scene_desc) and builds one
  * bounding volume hierarchy per mesh with default settings.  Invalidates
- * the reference state.  Errors: ARG (bad index, size or key order), OOM, CUDA. */
+ * the reference state.  Errors: ARG (bad index, size or key order), OOM, CUDA.
+ * Paper: the scenes of Sec. 4 (diffuse and glossy surfaces, area lights, an
+ * environment map, camera and object motion over time) that the path tracer
+ * of Sec. 3.1 / 3.3 renders. */
 mcev_status mcev_scene_upload(mcev_ctx* ctx, const mcev_scene_desc* desc);
 
 /* Rebuilds the per-mesh BVHs with a binned surface-area heuristic of
  * `sah_bins` bins (4..256) and leaves of at most `max_leaf` (1..16)
- * triangles.  Errors: ARG, STATE (no scene), OOM, CUDA. */
+ * triangles.  Errors: ARG, STATE (no scene), OOM, CUDA.
+ * No paper passage: the acceleration structure is the renderer's (the
+ * paper relies on pbrt-v4's, Sec. 3.3). */
 mcev_status mcev_build_bvh(mcev_ctx* ctx, int32_t sah_bins, int32_t max_leaf);
 
 /* Sets render settings (see mcev_params); a new bvh_width rebuilds the BVHs of
  * the uploaded scene.  Errors: ARG (the settings are unchanged), and OOM or
- * CUDA from that rebuild (the scene must then be uploaded again). */
+ * CUDA from that rebuild (the scene must then be uploaded again).
+ * Paper: eps is the dark level of the log samples (Sec. 3.1), spp_min the
+ * first test point (Sec. 3.3), variant and se_mode the test of Sec. 3.2 and
+ * its ablations (Table 2); the rest is infrastructure. */
 mcev_status mcev_set_params(mcev_ctx* ctx, const mcev_params* params);
 
 /* First frame of Alg. 1: renders every pixel at time t0 with spp samples and
  * stores (count, mean, M2) of ln(L + eps) as the reference state.  Errors:
- * ARG, STATE, OOM, CUDA. */
+ * ARG, STATE, OOM, CUDA, TIMEOUT.
+ * Paper: Alg. 1 (the reference frame rendered at the full sample count). */
 mcev_status mcev_render_reference(mcev_ctx* ctx, double t0, int32_t spp);
 
 /* One frame of Alg. 1 for the pair (t0, t1).  If the reference state is not
@@ -207,13 +231,21 @@ mcev_status mcev_render_reference(mcev_ctx* ctx, double t0, int32_t spp);
  *   spp_out    : device int32 [H*W] or NULL: samples used per pixel
  *   mean_out   : device float [H*W] or NULL: mean ln(L + eps) at t1
  *   stats_out  : host or NULL; filled when non-NULL
- * The call returns when the frame is done: each round reads the number of
- * undecided pixels back to the host to size the next round, so the stream is
- * synchronised several times per call.
+ * The call returns when the frame is done.  By default the rounds run on the
+ * device (one CUDA graph per call whose loop sizes every round from the
+ * number of pixels the previous one re-queued) and the stream is
+ * synchronised once at the end; with host_rounds = 1 (or profile = 1) every
+ * round reads that number back to the host instead.  If the device loop hits
+ * its bound the call returns MCEV_ERR_TIMEOUT: the outputs are incomplete and
+ * the reference state is invalidated (the next call renders it again), and
+ * the context stays usable.
  * Sample k of pixel p at time t uses the same random numbers in every mode,
  * so adaptive samples are a prefix of the uniform ones.
  * Errors: ARG (C < 0, alpha outside (0,1), spp_batch < 1, spp_max < spp_min,
- * spp_max above the wavefront), STATE, OOM, CUDA. */
+ * spp_max above the wavefront), STATE, OOM, CUDA, TIMEOUT.
+ * Paper: Alg. 1 (one frame of its loop), Sec. 3.1 (log-luminance samples),
+ * Sec. 3.2 and Eq. 7 (the t-test), Sec. 3.3 (batches and the cap), Eq. 1
+ * (the event rule). */
 mcev_status mcev_render_events(mcev_ctx* ctx, double t0, double t1, float C, float alpha,
                                int32_t spp_batch, int32_t spp_max, int8_t* events_out,
                                int32_t* spp_out, float* mean_out, mcev_stats* stats_out);
@@ -227,7 +259,8 @@ mcev_status mcev_render_events(mcev_ctx* ctx, double t0, double t1, float C, flo
  * ------------------------------------------------------------------------ */
 
 /* RGB albedo texture [height][width][3] (device float) used by textured
- * materials; NULL restores the materials' table albedo.  Errors: ARG. */
+ * materials; NULL restores the materials' table albedo.  Errors: ARG.
+ * No paper passage: the differentiable-rendering extension. */
 mcev_status mcev_set_texture(mcev_ctx* ctx, const float* texture, int32_t width, int32_t height);
 
 /* Emitted radiance per material (device float [n_materials]) overriding the
@@ -235,12 +268,15 @@ mcev_status mcev_set_texture(mcev_ctx* ctx, const float* texture, int32_t width,
  * entries of the other materials are ignored, since the set of emitters that
  * next-event estimation samples is fixed by the scene.  An override <= 0
  * turns that emitter dark.  NULL restores the table.
- * Errors: ARG (n != material count). */
+ * Errors: ARG (n != material count).
+ * No paper passage: the differentiable-rendering extension. */
 mcev_status mcev_set_emission(mcev_ctx* ctx, const float* emission, int32_t n_materials);
 
 /* Per-pixel mean of ln(L + eps) over samples 0..spp-1 at time t (every
  * pixel the same count; the reference state is not touched).
- *   mean_out: device float [H*W].  Errors: ARG, STATE, OOM, CUDA. */
+ *   mean_out: device float [H*W].  Errors: ARG, STATE, OOM, CUDA, TIMEOUT.
+ * Paper: the sample mean of log luminance of Sec. 3.1 at a fixed count; its
+ * use for gradients is the differentiable-rendering extension. */
 mcev_status mcev_render_mean(mcev_ctx* ctx, double t, int32_t spp, float* mean_out);
 
 /* Adjoint of mcev_render_mean (path-replay backpropagation): given
@@ -248,7 +284,8 @@ mcev_status mcev_render_mean(mcev_ctx* ctx, double t, int32_t spp, float* mean_o
  * RGB to grad_texture (device float [th][tw][3], may be NULL) and
  * d loss / d emitted radiance to grad_emission (device float [n_materials],
  * may be NULL), replaying the same samples with the same random numbers.
- * Errors: ARG, STATE, OOM, CUDA. */
+ * Errors: ARG, STATE, OOM, CUDA.
+ * No paper passage: the differentiable-rendering extension. */
 mcev_status mcev_backward(mcev_ctx* ctx, double t, int32_t spp, const float* grad_mean, float* grad_texture,
                           float* grad_emission);
 
@@ -272,7 +309,8 @@ typedef struct {
  * reported counters.  All jobs must share spp_min, variant and se_mode (the
  * schedule) and the BVH node layout (bvh_width); every other setting is per job.  Jobs must use distinct
  * contexts on the runner's device, of at most 2^24 pixels each; n_jobs is
- * 1..256.  Errors: ARG, STATE, OOM, CUDA. */
+ * 1..256.  Errors: ARG, STATE, OOM, CUDA, TIMEOUT.
+ * Paper: Alg. 1 per job; sharing rounds across jobs is infrastructure. */
 mcev_status mcev_render_events_batch(mcev_ctx* runner, const mcev_job* jobs, int32_t n_jobs, float C, float alpha,
                                      int32_t spp_batch, int32_t spp_max, mcev_stats* stats_out);
 
@@ -283,19 +321,24 @@ mcev_status mcev_render_events_batch(mcev_ctx* runner, const mcev_job* jobs, int
  *   sig_out: device uint32 [n_pix][count] or NULL: FNV-1a hash of every
  *            discrete decision along the path (hit instance/triangle ids,
  *            environment texel, emission, NEE, visibility and sampling flags)
- * Errors: ARG, STATE, OOM, CUDA. */
+ * Errors: ARG, STATE, OOM, CUDA.
+ * Paper: tracePaths of Alg. 1; the samples of Sec. 3.1. */
 mcev_status mcev_trace_samples(mcev_ctx* ctx, double t, const int32_t* pixels, int64_t n_pix,
                                int64_t k0, int32_t count, float* L_out, uint32_t* sig_out);
 
 /* Size in bytes of the reference-state blob: a 16-byte header (double
  * reference time, int32 valid flag, int32 pixel count) followed by int32
- * n[H*W], float mean[H*W], float M2[H*W]. */
+ * n[H*W], float mean[H*W], float M2[H*W].
+ * Paper: the reference statistics Alg. 1 carries from frame to frame; the
+ * blob format is infrastructure. */
 size_t mcev_state_bytes(const mcev_ctx* ctx);
 
 /* Copies the reference state (checkpoint) into a device buffer of
  * mcev_state_bytes() bytes; mcev_set_state restores it (resume).  The state
  * plus the reference time is all Alg. 1 carries between frames.
- * Errors: ARG (NULL or wrong size), CUDA. */
+ * Errors: ARG (NULL or wrong size), CUDA.
+ * Paper: Alg. 1 (the reference it keeps); checkpoint and resume are
+ * infrastructure. */
 mcev_status mcev_get_state(mcev_ctx* ctx, void* dev_buf, size_t bytes);
 mcev_status mcev_set_state(mcev_ctx* ctx, const void* dev_buf, size_t bytes);
 
@@ -421,7 +464,8 @@ typedef struct mcev_quality {
  * needs no scene; scratch (8 bytes per voxel, plus up to 2 GiB of envelope
  * stacks) is allocated through it.
  * Errors: ARG (NULL inputs, an extent outside 1..16384, tau2 < 0, a value
- * outside {-1, 0, 1}), OOM, CUDA. */
+ * outside {-1, 0, 1}), OOM, CUDA.
+ * Paper: the quality metrics of Sec. 4.2 (RMSE, PSNR, F1, PSCD). */
 mcev_status mcev_event_quality(mcev_ctx* ctx, const int8_t* a, const int8_t* b, int32_t width, int32_t height,
                                int32_t frames, int32_t tau2, int32_t* d2_a, int32_t* d2_b, mcev_quality* out);
 

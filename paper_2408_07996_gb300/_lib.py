@@ -43,7 +43,7 @@ class Params(C.Structure):
         ("eps", C.c_float), ("t_min", C.c_float), ("max_depth", C.c_int32), ("nee", C.c_int32),
         ("mis", C.c_int32), ("spp_min", C.c_int32), ("variant", C.c_int32), ("se_mode", C.c_int32),
         ("seed", C.c_uint64), ("wavefront", C.c_int64), ("profile", C.c_int32), ("batch_window", C.c_int32),
-        ("bvh_width", C.c_int32),
+        ("bvh_width", C.c_int32), ("host_rounds", C.c_int32), ("device_timeout_us", C.c_int32),
     ]
 
 

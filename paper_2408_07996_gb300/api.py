@@ -37,6 +37,8 @@ class RenderSettings:
     profile: int = 0
     batch_window: int = 0
     bvh_width: int = 0
+    host_rounds: int = 0
+    device_timeout_us: int = 0
 
 
 class Renderer:
@@ -155,7 +157,8 @@ class Renderer:
         s = replace(self.settings, **kw)
         p = L.Params(eps=s.eps, t_min=s.t_min, max_depth=s.max_depth, nee=s.nee, mis=s.mis,
                      spp_min=s.spp_min, variant=s.variant, se_mode=s.se_mode, seed=s.seed,
-                     wavefront=s.wavefront, profile=s.profile, batch_window=s.batch_window, bvh_width=s.bvh_width)
+                     wavefront=s.wavefront, profile=s.profile, batch_window=s.batch_window, bvh_width=s.bvh_width,
+                     host_rounds=s.host_rounds, device_timeout_us=s.device_timeout_us)
         L.check(self.lib.mcev_set_params(self.ctx, C.byref(p)), self.ctx, "mcev_set_params")
         self.settings = s
         return s

@@ -15,6 +15,8 @@
 #include <tuple>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/mcev.h"
 #include "bvh.h"
 #include "kernels.h"
@@ -23,6 +25,15 @@
 #include "tdist.h"
 
 using namespace mcev;
+
+// NVTX range for the lifetime of a scope (shows the library's calls, rounds
+// and chunks on an Nsight timeline; a no-op when no tool is attached)
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // BVH node layout used unless mcev_params.bvh_width asks for the other
 #ifndef MCEV_DEFAULT_BVH_WIDTH
@@ -116,6 +127,10 @@ struct mcev_ctx {
 
     // batched renders run by this context: job table and union queues
     DevBuf d_jobs, d_bqueue;
+
+    // device-resident round loop: its state and the stream graphs are captured on
+    DevBuf d_round;
+    cudaStream_t cap_stream = nullptr;
 
     // t critical values
     DevBuf d_tcrit;
@@ -799,16 +814,21 @@ struct BatchRun {
     bool wide = false;        // every job's BLAS use the wide layout
 };
 
-// one chunk of n_paths = nj * spp_r paths through every bounce
+// one chunk of n_paths = nj * spp_r paths through every bounce (with rc:
+// the current chunk of the device-resident round loop, n_paths then being
+// the wavefront capacity that sizes the launches)
 mcev_status trace_chunk(mcev_ctx* ctx, const Frame& fr, const DevParams& P, const int32_t* queue, int64_t j0,
-                        int32_t spp_r, int64_t k_base, int64_t n_paths, const BatchRun* B = nullptr) {
+                        int32_t spp_r, int64_t k_base, int64_t n_paths, const BatchRun* B = nullptr,
+                        const RoundCtl* rc = nullptr) {
     const Wave& w = ctx->wave;
     int32_t* err = ctx->wave.counters + 15;
     const Job* jobs = B ? B->d_jobs : nullptr;
     const int depth_max = B ? B->max_depth : P.max_depth;
     const bool nee = B ? B->any_nee : P.nee != 0;
     const bool wide = B ? B->wide : ctx->dsc.wide != 0;
-    LAUNCH(MCEV_K_RAYGEN, launch_raygen(fr.dev, P, w, queue, j0, spp_r, k_base, n_paths, 0, ctx->sms, ctx->stream, jobs));
+    NvtxRange range("mcev chunk");
+    LAUNCH(MCEV_K_RAYGEN,
+           launch_raygen(fr.dev, P, w, queue, j0, spp_r, k_base, n_paths, 0, ctx->sms, ctx->stream, jobs, rc));
     int cur = 0;
     LAUNCH(MCEV_K_EXTEND,
            launch_extend(ctx->dsc, fr.dev, P.t_min, w, cur, n_paths, err, ctx->sms, ctx->stream, jobs, wide));
@@ -836,11 +856,162 @@ mcev_status trace_chunk(mcev_ctx* ctx, const Frame& fr, const DevParams& P, cons
     return MCEV_OK;
 }
 
+// Default wall-clock bound of the device-resident round loop.
+constexpr int64_t kDefaultDeviceTimeoutUs = 300ll * 1000 * 1000;
+
+// The rounds of run_rounds as one CUDA graph on the device (see kernels.cu,
+// k_round_next): no host round trip until the frame is done.  The graph is
+// captured on the context's capture stream and launched on its stream.
+mcev_status run_rounds_device(mcev_ctx* ctx, const Frame& fr, StatsArgs A, int64_t* paths_out, int32_t* rounds_out,
+                              const BatchRun* B) {
+    NvtxRange range("mcev device round loop");
+    const DevParams P = dev_params(ctx, false);
+    int32_t* queue[2] = {ctx->queue[0], ctx->queue[1]};
+    int64_t Q0 = (int64_t)ctx->W * ctx->H;
+    if (B) {
+        queue[0] = B->queue[0];
+        queue[1] = B->queue[1];
+        Q0 = B->q0;
+    }
+    const Job* jobs = B ? B->d_jobs : nullptr;
+    ST(dev_alloc(ctx, ctx->d_round, sizeof(RoundCtl)));
+    RoundCtl* rc = (RoundCtl*)ctx->d_round.ptr;
+    if (!ctx->cap_stream) CU(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+    RoundPlan plan{};
+    plan.cap = ctx->wave.cap;
+    plan.Q0 = Q0;
+    plan.spp_min = A.spp_min;
+    plan.spp_batch = A.spp_batch;
+    plan.spp_max = A.spp_max;
+    plan.window_max = ctx->params.batch_window > 0 ? ctx->params.batch_window : 16;
+    const int64_t tus = ctx->params.device_timeout_us > 0 ? ctx->params.device_timeout_us : kDefaultDeviceTimeoutUs;
+    plan.timeout_ns = (unsigned long long)tus * 1000ull;
+    // chunks the schedule can need: rounds x chunks of the largest round
+    const int64_t first = std::min(A.spp_min, A.spp_max);
+    const int64_t rounds_max = 2 + (A.spp_max - first + A.spp_batch - 1) / std::max(1, A.spp_batch);
+    const int64_t spp_r_max = std::max<int64_t>(first, std::min<int64_t>((int64_t)plan.window_max * A.spp_batch,
+                                                                         A.spp_max));
+    const int64_t chunks_max = (Q0 + std::max<int64_t>(1, plan.cap / spp_r_max) - 1) /
+                               std::max<int64_t>(1, plan.cap / spp_r_max);
+    plan.max_iters = (int32_t)std::min<int64_t>(rounds_max * (chunks_max + 1) + 4, 0x7fffffff);
+    // one graph: init, then WHILE(chunk; round control)
+    cudaGraph_t graph = nullptr, body = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t cs = ctx->cap_stream;
+    cudaStream_t saved = ctx->stream;
+    const int32_t kc0[MCEV_K_CLASSES] = {ctx->kcount[0], ctx->kcount[1], ctx->kcount[2], ctx->kcount[3],
+                                          ctx->kcount[4]};
+    const int launches0 = ctx->launches;
+    int body_launches = 0;
+    int32_t body_kc[MCEV_K_CLASSES] = {0, 0, 0, 0, 0};
+    auto build = [&]() -> mcev_status {
+        CU(cudaGraphCreate(&graph, 0));
+        cudaGraphConditionalHandle h;
+        CU(cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault));
+        CU(cudaStreamBeginCaptureToGraph(cs, graph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        ctx->stream = cs;
+        mcev_status st = MCEV_OK;
+        cudaError_t e = launch_round_init(rc, ctx->wave, plan, queue[0], queue[1], B == nullptr, ctx->sms, cs);
+        cudaGraphNode_t cond = nullptr;
+        if (e == cudaSuccess) {
+            cudaStreamCaptureStatus cst;
+            cudaGraph_t g_out = nullptr;
+            const cudaGraphNode_t* deps = nullptr;
+            size_t ndeps = 0;
+            e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &g_out, &deps, nullptr, &ndeps);
+            if (e == cudaSuccess) {
+                cudaGraphNodeParams cp{};
+                cp.type = cudaGraphNodeTypeConditional;
+                cp.conditional.handle = h;
+                cp.conditional.type = cudaGraphCondTypeWhile;
+                cp.conditional.size = 1;
+                e = cudaGraphAddNode(&cond, g_out, deps, nullptr, ndeps, &cp);
+                if (e == cudaSuccess) {
+                    body = cp.conditional.phGraph_out[0];
+                    e = cudaStreamUpdateCaptureDependencies(cs, &cond, nullptr, 1, cudaStreamSetCaptureDependencies);
+                }
+            }
+        }
+        cudaGraph_t g2 = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(cs, &g2);
+        if (e != cudaSuccess || e2 != cudaSuccess) {
+            ctx->stream = saved;
+            cudaGetLastError();
+            return fail(ctx, MCEV_ERR_CUDA, "capturing the round loop failed: %s",
+                        cudaGetErrorString(e != cudaSuccess ? e : e2));
+        }
+        // the body: one chunk of every bounce, its statistics, the round control
+        CU(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        const int l0 = ctx->launches;
+        const int32_t k0[MCEV_K_CLASSES] = {ctx->kcount[0], ctx->kcount[1], ctx->kcount[2], ctx->kcount[3],
+                                             ctx->kcount[4]};
+        st = trace_chunk(ctx, fr, P, queue[0], 0, 1, 0, plan.cap, B, rc);
+        if (st == MCEV_OK) {
+            const cudaError_t el = launch_stats(ctx->wave, A, queue[0], 0, plan.cap, queue[1], ctx->sms, cs, jobs, rc);
+            if (el != cudaSuccess) st = fail(ctx, MCEV_ERR_CUDA, "launch stats failed: %s", cudaGetErrorString(el));
+            ++ctx->launches;
+            ++ctx->kcount[MCEV_K_STATS];
+        }
+        if (st == MCEV_OK) {
+            const cudaError_t el = launch_round_next(rc, ctx->wave, plan, h, cs);
+            if (el != cudaSuccess) st = fail(ctx, MCEV_ERR_CUDA, "launch round control failed: %s", cudaGetErrorString(el));
+            ++ctx->launches;
+            ++ctx->kcount[MCEV_K_STATS];
+        }
+        body_launches = ctx->launches - l0;
+        for (int i = 0; i < MCEV_K_CLASSES; ++i) body_kc[i] = ctx->kcount[i] - k0[i];
+        cudaGraph_t b2 = nullptr;
+        const cudaError_t e3 = cudaStreamEndCapture(cs, &b2);
+        ctx->stream = saved;
+        if (st != MCEV_OK) return st;
+        if (e3 != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ctx, MCEV_ERR_CUDA, "capturing the round body failed: %s", cudaGetErrorString(e3));
+        }
+        CU(cudaGraphInstantiate(&exec, graph, 0));
+        return MCEV_OK;
+    };
+    mcev_status st = build();
+    if (st == MCEV_OK) {
+        const cudaError_t e = cudaGraphLaunch(exec, ctx->stream);
+        if (e != cudaSuccess) st = fail(ctx, MCEV_ERR_CUDA, "cudaGraphLaunch failed: %s", cudaGetErrorString(e));
+    }
+    RoundCtl h_rc{};
+    if (st == MCEV_OK) {
+        const cudaError_t e1 = cudaMemcpyAsync(&h_rc, rc, sizeof h_rc, cudaMemcpyDeviceToHost, ctx->stream);
+        const cudaError_t e2 = e1 == cudaSuccess ? cudaStreamSynchronize(ctx->stream) : e1;
+        if (e2 != cudaSuccess) st = fail(ctx, MCEV_ERR_CUDA, "round loop failed: %s", cudaGetErrorString(e2));
+        ctx->d2h += (int64_t)sizeof h_rc;
+    }
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    // launches that ran: the init kernel plus the body once per chunk
+    ctx->launches = launches0 + 1 + body_launches * h_rc.iters;
+    for (int i = 0; i < MCEV_K_CLASSES; ++i) ctx->kcount[i] = kc0[i] + body_kc[i] * h_rc.iters;
+    ctx->kcount[MCEV_K_STATS] += 1;
+    if (st != MCEV_OK) return st;
+    ctx->stats_pix += h_rc.stats_pix;
+    if (h_rc.status == RC_TIMEOUT)
+        return fail(ctx, MCEV_ERR_TIMEOUT,
+                    "the device-resident round loop stopped after %d chunks (bound: %d chunks, %lld us); the "
+                    "frame is incomplete", h_rc.iters, plan.max_iters, (long long)tus);
+    if (h_rc.status == RC_CAP)
+        return fail(ctx, MCEV_ERR_STATE, "internal: %lld pixels undecided at the sample cap", (long long)h_rc.Q);
+    if (paths_out) *paths_out = h_rc.paths;
+    if (rounds_out) *rounds_out = h_rc.rounds;
+    return MCEV_OK;
+}
+
 // Runs rounds of batches over the pixel queue until no pixel is undecided.
 // mode REFERENCE: every pixel to spp_max samples, statistics -> ref.
 // mode DETECT: Alg. 1 frame with the test variant in `A`.
+// The rounds run on the device (one CUDA graph, run_rounds_device) unless
+// per-launch timing is on or the caller asked for host-driven rounds.
 mcev_status run_rounds(mcev_ctx* ctx, const Frame& fr, StatsArgs A, int64_t* paths_out, int32_t* rounds_out,
                        const BatchRun* B = nullptr) {
+    if (!ctx->params.profile && !ctx->params.host_rounds) return run_rounds_device(ctx, fr, A, paths_out, rounds_out, B);
+    NvtxRange range("mcev host rounds");
     const DevParams P = dev_params(ctx, false);
     int32_t* queue[2] = {ctx->queue[0], ctx->queue[1]};
     int64_t Q;
@@ -871,6 +1042,7 @@ mcev_status run_rounds(mcev_ctx* ctx, const Frame& fr, StatsArgs A, int64_t* pat
             m = std::min(std::min(m, left), window_max);
             spp_r = (int32_t)std::min<int64_t>(m * sub, A.spp_max - n_done);
         }
+        NvtxRange round_range("mcev round");
         CU(cudaMemsetAsync(ctx->wave.counters + 3, 0, sizeof(int32_t), ctx->stream));
         A.spp_r = spp_r;
         A.sub = sub;
@@ -879,7 +1051,8 @@ mcev_status run_rounds(mcev_ctx* ctx, const Frame& fr, StatsArgs A, int64_t* pat
         for (int64_t j0 = 0; j0 < Q; j0 += per_chunk) {
             const int64_t nj = std::min(per_chunk, Q - j0);
             ST(trace_chunk(ctx, fr, P, queue[qi], j0, spp_r, n_done, nj * spp_r, B));
-            LAUNCH(MCEV_K_STATS, launch_stats(ctx->wave, A, queue[qi], j0, nj, queue[qi ^ 1], ctx->sms, ctx->stream, jobs));
+            LAUNCH(MCEV_K_STATS,
+                   launch_stats(ctx->wave, A, queue[qi], j0, nj, queue[qi ^ 1], ctx->sms, ctx->stream, jobs, nullptr));
             ctx->stats_pix += nj;
         }
         paths += Q * spp_r;
@@ -959,6 +1132,8 @@ mcev_status check_ready(mcev_ctx* ctx) {
 }
 
 mcev_status do_reference(mcev_ctx* ctx, double t0, int32_t spp, int64_t* paths) {
+    NvtxRange range("mcev reference frame");
+    ctx->ref_valid = false;   // overwritten from here on; valid again only when complete
     ST(frame_setup(ctx, t0, 0));
     StatsArgs A{};
     A.cur = ctx->cur;
@@ -1022,8 +1197,10 @@ void mcev_destroy(mcev_ctx* ctx) {
     cudaStreamSynchronize(ctx->stream);
     DevBuf* bufs[] = {&ctx->d_nodes, &ctx->d_wnodes, &ctx->d_tris, &ctx->d_uv, &ctx->d_mats, &ctx->d_env, &ctx->d_marg, &ctx->d_cond,
                       &ctx->d_tpdf, &ctx->frames[0].buf, &ctx->frames[1].buf, &ctx->d_wave, &ctx->d_counters,
-                      &ctx->d_pix, &ctx->d_tcrit, &ctx->d_jobs, &ctx->d_bqueue, &ctx->d_quality, &ctx->d_gemit};
+                      &ctx->d_pix, &ctx->d_tcrit, &ctx->d_jobs, &ctx->d_bqueue, &ctx->d_quality, &ctx->d_gemit,
+                      &ctx->d_round};
     for (DevBuf* b : bufs) dev_free(ctx, *b);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     for (cudaEvent_t e : ctx->evpool) cudaEventDestroy(e);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
@@ -1050,6 +1227,7 @@ mcev_status mcev_set_allocator(mcev_ctx* ctx, mcev_alloc_fn alloc, mcev_free_fn 
 }
 
 mcev_status mcev_scene_upload(mcev_ctx* ctx, const mcev_scene_desc* s) {
+    NvtxRange range("mcev_scene_upload");
     if (!ctx) return MCEV_ERR_ARG;
     if (!s) return fail(ctx, MCEV_ERR_ARG, "null scene description");
     if (s->n_triangles < 0 || s->n_vertices < 0 || s->n_meshes < 0 || s->n_instances < 0 || s->n_keys < 1 ||
@@ -1187,7 +1365,8 @@ mcev_status mcev_set_params(mcev_ctx* ctx, const mcev_params* p) {
         p->variant < 0 || p->variant > 3 || p->se_mode < 0 || p->se_mode > 1 || p->wavefront < 0 ||
         p->batch_window < 0 || p->batch_window > 1024 ||
         (p->wavefront > 0 && p->wavefront < 1024) || p->wavefront > ((int64_t)1 << 30) ||
-        (p->bvh_width != 0 && p->bvh_width != 2 && p->bvh_width != 8))
+        (p->bvh_width != 0 && p->bvh_width != 2 && p->bvh_width != 8) || p->host_rounds < 0 ||
+        p->host_rounds > 1 || p->device_timeout_us < 0)
         return fail(ctx, MCEV_ERR_ARG, "invalid render parameters");
     const bool reseed = p->seed != ctx->params.seed;
     const bool shape = p->eps != ctx->params.eps || p->t_min != ctx->params.t_min ||
@@ -1223,6 +1402,7 @@ mcev_status mcev_render_reference(mcev_ctx* ctx, double t0, int32_t spp) {
 mcev_status mcev_render_events(mcev_ctx* ctx, double t0, double t1, float C, float alpha, int32_t spp_batch,
                                int32_t spp_max, int8_t* events_out, int32_t* spp_out, float* mean_out,
                                mcev_stats* stats_out) {
+    NvtxRange range("mcev_render_events");
     ST(check_ready(ctx));
     if (!events_out) return fail(ctx, MCEV_ERR_ARG, "events_out is required");
     if (!(C >= 0.0f) || !(alpha > 0.0f && alpha < 1.0f) || spp_batch < 1 || spp_max < ctx->params.spp_min)
@@ -1251,7 +1431,11 @@ mcev_status mcev_render_events(mcev_ctx* ctx, double t0, double t1, float C, flo
     A.mode = MODE_DETECT;
     A.variant = ctx->params.variant;
     A.se_mode = ctx->params.se_mode;
-    ST(run_rounds(ctx, ctx->frames[1], A, &paths, &rounds));
+    const mcev_status rs = run_rounds(ctx, ctx->frames[1], A, &paths, &rounds);
+    if (rs != MCEV_OK) {
+        ctx->ref_valid = false;   // some pixels may have updated their reference already
+        return rs;
+    }
     ctx->ref_valid = true;
     ctx->ref_time = t1;
     CU(cudaEventRecord(ctx->ev1, ctx->stream));
@@ -1299,6 +1483,7 @@ mcev_status mcev_set_emission(mcev_ctx* ctx, const float* emission, int32_t n_ma
 }
 
 mcev_status mcev_render_mean(mcev_ctx* ctx, double t, int32_t spp, float* mean_out) {
+    NvtxRange range("mcev_render_mean");
     ST(check_ready(ctx));
     if (spp < 1 || !mean_out) return fail(ctx, MCEV_ERR_ARG, "need spp >= 1 and mean_out");
     ST(check_spp_fits(ctx, spp));
@@ -1316,6 +1501,7 @@ mcev_status mcev_render_mean(mcev_ctx* ctx, double t, int32_t spp, float* mean_o
 
 mcev_status mcev_backward(mcev_ctx* ctx, double t, int32_t spp, const float* grad_mean, float* grad_texture,
                           float* grad_emission) {
+    NvtxRange range("mcev_backward");
     ST(check_ready(ctx));
     if (spp < 1 || !grad_mean) return fail(ctx, MCEV_ERR_ARG, "need spp >= 1 and grad_mean");
     ST(check_spp_fits(ctx, spp));
@@ -1353,6 +1539,7 @@ mcev_status mcev_backward(mcev_ctx* ctx, double t, int32_t spp, const float* gra
 
 mcev_status mcev_render_events_batch(mcev_ctx* runner, const mcev_job* jobs, int32_t n_jobs, float C, float alpha,
                                      int32_t spp_batch, int32_t spp_max, mcev_stats* stats_out) {
+    NvtxRange range("mcev_render_events_batch");
     mcev_ctx* ctx = runner;
     if (!ctx) return MCEV_ERR_ARG;
     if (!jobs || n_jobs < 1 || n_jobs > 256) return fail(ctx, MCEV_ERR_ARG, "need 1..256 jobs");
@@ -1437,6 +1624,7 @@ mcev_status mcev_render_events_batch(mcev_ctx* runner, const mcev_job* jobs, int
         StatsArgs R{};
         R.spp_min = R.spp_batch = R.spp_max = spp_max;
         R.mode = MODE_REFERENCE;
+        for (int i : need) jobs[i].ctx->ref_valid = false;
         ST(run_rounds(ctx, ctx->frames[0], R, &ref_paths, nullptr, &B));
         for (int i : need) {
             jobs[i].ctx->ref_valid = true;
@@ -1459,7 +1647,11 @@ mcev_status mcev_render_events_batch(mcev_ctx* runner, const mcev_job* jobs, int
     A.mode = MODE_DETECT;
     A.variant = variant;
     A.se_mode = se_mode;
-    ST(run_rounds(ctx, ctx->frames[1], A, &paths, &rounds, &B));
+    const mcev_status rs = run_rounds(ctx, ctx->frames[1], A, &paths, &rounds, &B);
+    if (rs != MCEV_OK) {
+        for (int i = 0; i < n_jobs; ++i) jobs[i].ctx->ref_valid = false;
+        return rs;
+    }
     for (int i = 0; i < n_jobs; ++i) {
         jobs[i].ctx->ref_valid = true;
         jobs[i].ctx->ref_time = jobs[i].t1;

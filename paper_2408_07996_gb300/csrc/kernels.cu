@@ -52,7 +52,15 @@ static constexpr uint32_t FNV_BASIS = 2166136261u;
 template <bool kBatch>
 __global__ void __launch_bounds__(256) k_raygen(DevFrame fr, DevParams P, Wave w, const int32_t* __restrict__ queue,
                                                 int64_t j0, int32_t spp_r, int64_t k_base, int64_t n_paths, int cur,
-                                                const Job* __restrict__ jobs) {
+                                                const Job* __restrict__ jobs, const RoundCtl* __restrict__ rc) {
+    if (rc) {
+        // sizes of the current chunk of the device-resident round loop
+        queue = rc->queue[rc->qi];
+        j0 = rc->j0;
+        spp_r = rc->spp_r;
+        k_base = rc->n_done;
+        n_paths = rc->nj * (int64_t)rc->spp_r;
+    }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         w.counters[cur] = (int32_t)n_paths;
         w.counters[1 - cur] = 0;
@@ -444,7 +452,17 @@ __device__ __forceinline__ Moments chan(Moments a, Moments b) {
 template <bool kChecked, bool kBatch>
 __global__ void __launch_bounds__(256) k_stats(Wave w, StatsArgs A0, const int32_t* __restrict__ queue, int64_t j0,
                                                int64_t n_pix, int32_t* __restrict__ next_queue,
-                                               const Job* __restrict__ jobs) {
+                                               const Job* __restrict__ jobs, const RoundCtl* __restrict__ rc) {
+    if (rc) {
+        // sizes of the current chunk of the device-resident round loop
+        queue = rc->queue[rc->qi];
+        next_queue = rc->queue[rc->qi ^ 1];
+        j0 = rc->j0;
+        n_pix = rc->nj;
+        A0.spp_r = rc->spp_r;
+        A0.sub = rc->sub;
+        A0.k_base = rc->n_done;
+    }
     const int lane = threadIdx.x & 31;
     const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -616,13 +634,14 @@ static int grid_for(int64_t work, int block, int sms, int per_sm) {
 
 cudaError_t launch_raygen(const DevFrame& fr, const DevParams& P, const Wave& w, const int32_t* queue, int64_t j0,
                           int32_t spp_r, int64_t k_base, int64_t n_paths, int cur, int sms, cudaStream_t st,
-                          const Job* jobs) {
+                          const Job* jobs, const RoundCtl* rc) {
+    // with rc, n_paths is the wavefront capacity (the chunk's size is on the device)
     if (jobs)
         k_raygen<true><<<grid_for(n_paths, 256, sms, 16), 256, 0, st>>>(fr, P, w, queue, j0, spp_r, k_base, n_paths,
-                                                                          cur, jobs);
+                                                                          cur, jobs, rc);
     else
         k_raygen<false><<<grid_for(n_paths, 256, sms, 16), 256, 0, st>>>(fr, P, w, queue, j0, spp_r, k_base, n_paths,
-                                                                           cur, nullptr);
+                                                                           cur, nullptr, rc);
     return cudaGetLastError();
 }
 
@@ -664,20 +683,115 @@ cudaError_t launch_shadow_extend(const DevScene& sc, const DevFrame& fr, const D
 }
 
 cudaError_t launch_stats(const Wave& w, const StatsArgs& A, const int32_t* queue, int64_t j0, int64_t n_pix,
-                         int32_t* next_queue, int sms, cudaStream_t st, const Job* jobs) {
+                         int32_t* next_queue, int sms, cudaStream_t st, const Job* jobs, const RoundCtl* rc) {
+    // with rc, n_pix is an upper bound of the chunk's pixels (the size is on the device)
     if (jobs)
         k_stats<false, true><<<grid_for(n_pix * 32, 256, sms, 8), 256, 0, st>>>(w, A, queue, j0, n_pix, next_queue,
-                                                                                 jobs);
+                                                                                 jobs, rc);
     else
         k_stats<false, false><<<grid_for(n_pix * 32, 256, sms, 8), 256, 0, st>>>(w, A, queue, j0, n_pix, next_queue,
-                                                                                  nullptr);
+                                                                                  nullptr, rc);
     return cudaGetLastError();
 }
 
 static cudaError_t launch_stats_checked(const Wave& w, const StatsArgs& A, const int32_t* queue, int64_t n_pix,
                                         int32_t* next_queue, int sms, cudaStream_t st) {
     k_stats<true, false><<<grid_for(n_pix * 32, 256, sms, 8), 256, 0, st>>>(w, A, queue, 0, n_pix, next_queue,
-                                                                             nullptr);
+                                                                             nullptr, nullptr);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ device-resident round loop
+// The rounds of Alg. 1's sampling schedule (Sec. 3.3) without the host: a
+// CUDA graph runs k_round_init, then a conditional WHILE node whose body is
+// one wavefront chunk (raygen, bounces, statistics) followed by
+// k_round_next, which moves to the next chunk of the round or, at the end
+// of a round, reads the number of re-queued pixels and sizes the next round
+// (first round spp_min samples, then windows of spp_batch batches that fill
+// the wavefront), and clears the condition when no pixel is left.  The loop
+// is bounded: after plan.max_iters chunks, or plan.timeout_ns of wall clock
+// (%globaltimer), it stops with RC_TIMEOUT, which the host reports as
+// MCEV_ERR_TIMEOUT.
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void round_first_chunk(RoundCtl* rc, const RoundPlan& plan) {
+    rc->per_chunk = max((int64_t)1, plan.cap / rc->spp_r);
+    rc->j0 = 0;
+    rc->nj = min(rc->per_chunk, rc->Q);
+}
+
+__global__ void k_round_init(RoundCtl* rc, Wave w, RoundPlan plan, int32_t* q0, int32_t* q1, int iota) {
+    if (iota)
+        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < plan.Q0; i += (int64_t)gridDim.x * blockDim.x)
+            q0[i] = (int32_t)i;
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    rc->queue[0] = q0;
+    rc->queue[1] = q1;
+    rc->Q = plan.Q0;
+    rc->n_done = 0;
+    rc->paths = 0;
+    rc->stats_pix = 0;
+    rc->qi = 0;
+    rc->rounds = 0;
+    rc->iters = 0;
+    rc->status = RC_OK;
+    rc->spp_r = rc->sub = min(plan.spp_min, plan.spp_max);
+    round_first_chunk(rc, plan);
+    w.counters[3] = 0;
+    rc->t_start = global_ns();
+}
+
+__global__ void k_round_next(RoundCtl* rc, Wave w, RoundPlan plan, cudaGraphConditionalHandle h) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    rc->iters += 1;
+    rc->stats_pix += rc->nj;
+    unsigned int go = 1;
+    if (rc->iters >= plan.max_iters || global_ns() - rc->t_start > plan.timeout_ns) {
+        rc->status = RC_TIMEOUT;
+        go = 0;
+    } else if (rc->j0 + rc->per_chunk < rc->Q) {
+        rc->j0 += rc->per_chunk;
+        rc->nj = min(rc->per_chunk, rc->Q - rc->j0);
+    } else {
+        // the round is done: its undecided pixels form the next round
+        rc->paths += rc->Q * (int64_t)rc->spp_r;
+        rc->n_done += rc->spp_r;
+        rc->rounds += 1;
+        const int32_t q = *(volatile int32_t*)(w.counters + 3);
+        w.counters[3] = 0;
+        rc->qi ^= 1;
+        rc->Q = q;
+        if (q == 0) {
+            go = 0;
+        } else if (rc->n_done >= plan.spp_max) {
+            rc->status = RC_CAP;
+            go = 0;
+        } else {
+            const int64_t sub = plan.spp_batch;
+            const int64_t left = (plan.spp_max - rc->n_done + sub - 1) / sub;
+            int64_t m = max((int64_t)1, plan.cap / max((int64_t)1, (int64_t)q * sub));
+            m = min(min(m, left), (int64_t)plan.window_max);
+            rc->sub = (int32_t)sub;
+            rc->spp_r = (int32_t)min(m * sub, (int64_t)plan.spp_max - rc->n_done);
+            round_first_chunk(rc, plan);
+        }
+    }
+    cudaGraphSetConditional(h, go);
+}
+
+cudaError_t launch_round_init(RoundCtl* rc, const Wave& w, const RoundPlan& plan, int32_t* q0, int32_t* q1,
+                              bool iota, int sms, cudaStream_t st) {
+    k_round_init<<<iota ? grid_for(plan.Q0, 256, sms, 8) : 1, 256, 0, st>>>(rc, w, plan, q0, q1, iota ? 1 : 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_round_next(RoundCtl* rc, const Wave& w, const RoundPlan& plan, cudaGraphConditionalHandle h,
+                              cudaStream_t st) {
+    k_round_next<<<1, 32, 0, st>>>(rc, w, plan, h);
     return cudaGetLastError();
 }
 
