@@ -266,7 +266,7 @@ def run_batch(args):
     if not args.no_tune:
         tune = tune_batch(runner, rs, (times[Wm], times[Wm + 1]), sched,
                           wavefronts=(1 << 25,), windows=(16,), leaf_sizes=(2, 4), bvh_widths=(2, 8))
-        tune = {"best": tune["best"], "trials": len(tune["trials"]), "jobs": len(rs)}
+        tune = {"best": tune["best"], "trials": tune["trials"], "jobs": len(rs)}
     torch.cuda.synchronize()
     clocks = Clocks(0)
     clocks.start()
@@ -328,16 +328,19 @@ STATS_BYTES_PER_PATH = 4
 QUALITY_BYTES_PER_EVENT = 4
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per traced ray of
-# the traversal launches, from the ncu capture of the terrain band recorded in
-# profiles/; None while the traversal kernels differ from the captured build.
-TRAVERSAL_DRAM_BYTES_PER_RAY = None
+# the traversal launches (k_extend + k_shadow_extend, two-wide BVH), from a
+# one-pass ncu capture of every launch of one timed terrain frame
+# (profiles/launches_terrain720p_timed_frame.md: 318.6 GB over 294 launches
+# that traced 3.852 G closest-hit and shadow rays); set to None when the
+# traversal kernels change.
+TRAVERSAL_DRAM_BYTES_PER_RAY = 82.71
 
 
-def traversal_traffic(rays_per_launch: float):
+def traversal_traffic(rays_per_launch: float, bvh_width: int = 2):
     """DRAM bytes of an average traversal launch: the captured bytes per ray
-    scaled by the rays an average timed launch traces (traffic grows with the
-    rays, as the captured launches show), or None."""
-    if TRAVERSAL_DRAM_BYTES_PER_RAY is None:
+    scaled by the rays an average timed launch traces, or None (no capture
+    of this layout's kernels)."""
+    if TRAVERSAL_DRAM_BYTES_PER_RAY is None or bvh_width == 8:
         return None
     return TRAVERSAL_DRAM_BYTES_PER_RAY * rays_per_launch
 
@@ -619,7 +622,9 @@ def main():
     roofline = {"kernel": "BVH traversal: k_extend, k_shadow_extend (closest-hit + shadow rays)", "bound": "alu",
                 "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": (achieved / peak_tflops) if achieved else None,
-                "traffic": traversal_traffic(rays / n_trav),
+                "traffic": traversal_traffic(rays / n_trav, args.bvh_width),
+                "traffic_basis": "DRAM bytes per traced ray from the ncu capture of a timed frame "
+                                 f"({TRAVERSAL_DRAM_BYTES_PER_RAY} B/ray) x rays per average launch",
                 "avg_launch_ms": ext_ms / n_trav, "launches": n_trav,
                 "flop_per_launch": flop / n_trav,
                 "box_tests_per_launch": boxes / n_trav, "tri_tests_per_launch": tris / n_trav,

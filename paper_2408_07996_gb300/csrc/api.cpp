@@ -111,7 +111,7 @@ struct mcev_ctx {
     // device scene
     DevBuf d_quality;                       // event-quality scratch: two int32 volumes + accumulators
     DevBuf d_gemit;                         // FP64 emission-gradient accumulator of mcev_backward
-    DevBuf d_nodes, d_wnodes, d_tris, d_uv, d_mats, d_env, d_marg, d_cond, d_tpdf;
+    DevBuf d_nodes, d_wnodes, d_tris, d_tshade, d_uv, d_mats, d_env, d_marg, d_cond, d_tpdf;
     DevScene dsc{};
     Frame frames[2];
 
@@ -451,6 +451,19 @@ mcev_status build_blas(mcev_ctx* ctx) {
     ctx->dsc.wnodes = (const uint4*)ctx->d_wnodes.ptr;
     ctx->dsc.wide = ctx->bvh_width == 8 ? 1 : 0;
     ST(upload(ctx, ctx->d_tris, tris.data(), tris.size() * sizeof(float4)));
+    // shading records: the (object-space) edge cross product (v1 - v0) x (v2 - v0) of
+    // each triangle's FP32 vertices, evaluated in FP64 and rounded, and its material
+    std::vector<float4> tsh(tris.size() / 3);
+    for (size_t t = 0; t < tsh.size(); ++t) {
+        const float4 a = tris[3 * t], b = tris[3 * t + 1], c = tris[3 * t + 2];
+        const double e1[3] = {(double)b.x - a.x, (double)b.y - a.y, (double)b.z - a.z};
+        const double e2[3] = {(double)c.x - a.x, (double)c.y - a.y, (double)c.z - a.z};
+        double cr[3];
+        cross(e1, e2, cr);
+        tsh[t] = make_float4((float)cr[0], (float)cr[1], (float)cr[2], b.w);
+    }
+    ST(upload(ctx, ctx->d_tshade, tsh.data(), tsh.size() * sizeof(float4)));
+    ctx->dsc.tshade = (const float4*)ctx->d_tshade.ptr;
     ctx->dsc.nodes = (const Node*)ctx->d_nodes.ptr;
     ctx->dsc.tris = (const float4*)ctx->d_tris.ptr;
     if (!ctx->tri_uv.empty()) {
@@ -1195,7 +1208,7 @@ void mcev_destroy(mcev_ctx* ctx) {
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
-    DevBuf* bufs[] = {&ctx->d_nodes, &ctx->d_wnodes, &ctx->d_tris, &ctx->d_uv, &ctx->d_mats, &ctx->d_env, &ctx->d_marg, &ctx->d_cond,
+    DevBuf* bufs[] = {&ctx->d_nodes, &ctx->d_wnodes, &ctx->d_tris, &ctx->d_tshade, &ctx->d_uv, &ctx->d_mats, &ctx->d_env, &ctx->d_marg, &ctx->d_cond,
                       &ctx->d_tpdf, &ctx->frames[0].buf, &ctx->frames[1].buf, &ctx->d_wave, &ctx->d_counters,
                       &ctx->d_pix, &ctx->d_tcrit, &ctx->d_jobs, &ctx->d_bqueue, &ctx->d_quality, &ctx->d_gemit,
                       &ctx->d_round};

@@ -181,7 +181,10 @@ __global__ void MCEV_SHADE_BOUNDS k_shade(DevScene sc, DevFrame fr, DevParams P,
         const int inst = __float_as_int(hv.y);
         const float4 rs = w.ray_s[cur][i];
         float beta = rs.x;
-        float L = w.L[p];
+        // radiance this vertex adds to the path (emission on a hit, the
+        // environment on a miss); the path's total is updated only when
+        // something is added
+        float Ladd = 0.0f;
         const float pdf_prev = rs.y;
         float pdf_next = 0.0f;
         uint32_t sig = 0, pflags = NO_FLAGS;
@@ -206,29 +209,29 @@ __global__ void MCEV_SHADE_BOUNDS k_shade(DevScene sc, DevFrame fr, DevParams P,
                 const float Le = __ldg(S.env + (int64_t)row * S.env_w + col);
                 float wgt = 1.0f;
                 if (depth > 0 && Q.nee) wgt = Q.mis ? power_heuristic(pdf_prev, F.p_env * texel_pdf(S, row, col, st)) : 0.0f;
-                L += beta * wgt * Le;
+                Ladd = beta * wgt * Le;
             } else if (Q.want_sig) {
                 sig = fnv(sig, 0xFFFFFFFEu);
             }
         } else {
             const int tri = __float_as_int(hv.z);
+            // the shading record (edge cross product, material) serves most
+            // hits; the vertices are read only for textured albedo, emitter
+            // MIS weights and the decision signature
+            const float4 tsh = __ldg(S.tshade + tri);
             const float4* tp = S.tris + 3 * tri;
-            const float4 q0 = __ldg(tp), q1 = __ldg(tp + 1), q2 = __ldg(tp + 2);
             const float4* ip = F.inst + 7 * __float_as_int(hv.w);
-            const float4 m0 = __ldg(ip), m1 = __ldg(ip + 1), m2 = __ldg(ip + 2);
             const float4 i0 = __ldg(ip + 3), i1 = __ldg(ip + 4), i2 = __ldg(ip + 5);
             const int ovr = __float_as_int(__ldg(ip + 6).y);
             if (Q.want_sig) {
                 sig = fnv(sig, (uint32_t)inst);
-                sig = fnv(sig, (uint32_t)__float_as_int(q0.w));
+                sig = fnv(sig, (uint32_t)__float_as_int(__ldg(tp).w));
             }
             const float t = hv.x;
             P0 = xyz(ro) + d * t;
-            const f3 e1 = xyz(q1) - xyz(q0), e2 = xyz(q2) - xyz(q0);
-            const f3 cr = cross3(e1, e2);
-            const f3 ng = norm3(xf_normal(i0, i1, i2, cr));
+            const f3 ng = norm3(xf_normal(i0, i1, i2, xyz(tsh)));
             const f3 wo = d * -1.0f;
-            const int mat = ovr >= 0 ? ovr : __float_as_int(q1.w);
+            const int mat = ovr >= 0 ? ovr : __float_as_int(tsh.w);
             const float4 mv = __ldg(S.mats + mat);
             const int tword = __float_as_int(mv.x);
             const int type = tword & 0xFF;
@@ -239,6 +242,7 @@ __global__ void MCEV_SHADE_BOUNDS k_shade(DevScene sc, DevFrame fr, DevParams P,
             int texel = -1;
             if ((tword & MAT_TEXTURED) && S.tex && S.tri_uv) {
                 // albedo = luminance of the nearest texel at the hit's texture coordinates
+                const float4 q0 = __ldg(tp), q1 = __ldg(tp + 1), q2 = __ldg(tp + 2);
                 float b1, b2;
                 barycentric(xf_point(i0, i1, i2, P0), xyz(q0), xyz(q1), xyz(q2), b1, b2);
                 const float b0 = 1.0f - b1 - b2;
@@ -259,6 +263,9 @@ __global__ void MCEV_SHADE_BOUNDS k_shade(DevScene sc, DevFrame fr, DevParams P,
                     if (!Q.mis) {
                         wgt = 0.0f;
                     } else {
+                        const float4 q0 = __ldg(tp), q1 = __ldg(tp + 1), q2 = __ldg(tp + 2);
+                        const float4 m0 = __ldg(ip), m1 = __ldg(ip + 1), m2 = __ldg(ip + 2);
+                        const f3 e1 = xyz(q1) - xyz(q0), e2 = xyz(q2) - xyz(q0);
                         const f3 we1 = xf_vec(m0, m1, m2, e1), we2 = xf_vec(m0, m1, m2, e2);
                         const f3 wc = cross3(we1, we2);
                         const float area = 0.5f * sqrtf(dot3(wc, wc));
@@ -266,13 +273,13 @@ __global__ void MCEV_SHADE_BOUNDS k_shade(DevScene sc, DevFrame fr, DevParams P,
                         wgt = power_heuristic(pdf_prev, pl);
                     }
                 }
-                L += beta * wgt * emit;
+                Ladd = beta * wgt * emit;
                 if (Q.adjoint && Q.grad_emit) atomicAdd(Q.grad_emit + mat, (double)(dlt * beta * wgt));
             }
             if (depth < Q.max_depth && alb > 0.0f) {
                 // adjoint: every contribution after this vertex carries one factor of its albedo
                 if (Q.adjoint && texel >= 0 && Q.grad_tex && dlt != 0.0f) {
-                    const float g = dlt * (w.Ltot[p] - L) / alb;
+                    const float g = dlt * (w.Ltot[p] - (w.L[p] + Ladd)) / alb;
                     float* gt = Q.grad_tex + 3 * (int64_t)texel;
                     atomicAdd(gt, g * MCEV_Y_R);
                     atomicAdd(gt + 1, g * MCEV_Y_G);
@@ -345,7 +352,7 @@ __global__ void MCEV_SHADE_BOUNDS k_shade(DevScene sc, DevFrame fr, DevParams P,
             }
             pflags = flags;
         }
-        w.L[p] = L;
+        if (Ladd != 0.0f) w.L[p] += Ladd;
         if (Q.want_sig) {
             w.sig[p] = sig;
             w.pflags[p] = pflags;
@@ -370,6 +377,13 @@ __global__ void MCEV_SHADE_BOUNDS k_shade(DevScene sc, DevFrame fr, DevParams P,
 }
 
 // ------------------------------------------------------------------ shadow rays
+// the light sample of shadow ray i reaches path p: add its contribution
+__device__ __forceinline__ void shadow_unoccluded(const Wave& w, const DevParams& Q, int i, int p) {
+    w.L[p] += w.sh_c[i];
+    if (Q.want_sig) w.pflags[p] |= 4u;
+    if (Q.adjoint && Q.grad_emit && w.sh_m[i] >= 0) atomicAdd(Q.grad_emit + w.sh_m[i], (double)(w.delta[p] * w.sh_g[i]));
+}
+
 // Shadow rays appended by shade(cur), indices first, first + stride, ...
 template <bool kBatch, bool kWide>
 __device__ __forceinline__ void shadow_rays(const DevScene& sc, const DevFrame& fr, const DevParams& P,
@@ -387,12 +401,7 @@ __device__ __forceinline__ void shadow_rays(const DevScene& sc, const DevFrame& 
         const DevScene& S = kBatch ? jobs[job].sc : sc;
         const DevFrame& F = kBatch ? jobs[job].fr : fr;
         const DevParams& Q = kBatch ? jobs[job].P : P;
-        if (!occluded<kWide>(S, F, xyz(o), xyz(d), Q.t_min, d.w, &e, work)) {
-            w.L[p] += w.sh_c[i];
-            if (Q.want_sig) w.pflags[p] |= 4u;
-            if (Q.adjoint && Q.grad_emit && w.sh_m[i] >= 0)
-                atomicAdd(Q.grad_emit + w.sh_m[i], (double)(w.delta[p] * w.sh_g[i]));
-        }
+        if (!occluded<kWide>(S, F, xyz(o), xyz(d), Q.t_min, d.w, &e, work)) shadow_unoccluded(w, Q, (int)i, p);
     }
     if (e) atomicOr(err, 1);
     add_work<kWide>(w, WORK_SHADOW, work);

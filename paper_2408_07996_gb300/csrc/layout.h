@@ -82,6 +82,7 @@ struct DevScene {
     const uint4* wnodes;      // BLAS nodes of every mesh (compressed 8-wide layout: 5 uint4 per node)
     int32_t wide;             // 1: the BLAS roots index `wnodes`
     const float4* tris;       // 3 float4 per triangle, leaf order
+    const float4* tshade;     // per triangle, leaf order: object-space (v1-v0)x(v2-v0), material (int bits)
     const float4* mats;       // (type, albedo, rough, emit)
     const float* env;         // [eh][ew] radiance
     const float* env_marg;    // [eh + 1] row CDF
