@@ -55,3 +55,26 @@ def tune_batch(runner: Renderer, renderers: list, pair: tuple, schedule: dict, w
     for r, s in zip(renderers, states):
         r.set_state(s)
     return {"best": best, "trials": trials}
+
+
+def tune_renderer(r: Renderer, pair: tuple, schedule: dict, bvh_widths=BVH_WIDTHS, leaf_sizes=LEAF_SIZES,
+                  sah_bins: int = 32) -> dict:
+    """The same search for one context: times the frame `pair` = (t0, t1)
+    for every BVH node layout and leaf size from the same reference state
+    and leaves the fastest applied (the reference state is restored, so
+    tuning does not advance the frame sequence).  `schedule` holds C, alpha,
+    spp_batch, spp_max."""
+    state = r.get_state().clone()
+    trials = []
+    for width, leaf in itertools.product(bvh_widths, leaf_sizes):
+        r.set_params(bvh_width=width)
+        r.build_bvh(sah_bins, leaf)
+        r.set_state(state)
+        st = r.render_events(pair[0], pair[1], schedule["C"], schedule["alpha"], schedule["spp_batch"],
+                             schedule["spp_max"])["stats"]
+        trials.append({"bvh_width": width, "max_leaf": leaf, "gpu_ms": st["gpu_ms"]})
+    best = min(trials, key=lambda t: t["gpu_ms"])
+    r.set_params(bvh_width=best["bvh_width"])
+    r.build_bvh(sah_bins, best["max_leaf"])
+    r.set_state(state)
+    return {"best": best, "trials": trials}
