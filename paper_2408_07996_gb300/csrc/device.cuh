@@ -342,124 +342,6 @@ __device__ __forceinline__ bool better_hit(float t, int inst, int prim, const Hi
 #define MCEV_ANY_ORDERED 1
 #endif
 
-// One node of a closest-hit BLAS traversal: tests both children, intersects
-// leaf triangles, and moves `node` to the next node (nearer child first,
-// farther one pushed).  Returns false when the traversal has finished.
-// rec: instance record; inst: its uploaded instance id, or -1 for the merged
-// static geometry whose triangles carry their own instance id (v2.w).
-__device__ __forceinline__ bool step_closest(const DevScene& sc, int rec, int inst, const WRay& r, float tmin,
-                                             Hit& h, int* stack, int base, int& sp, int& node, int* err,
-                                             int3& work) {
-    const Node n = load_node(sc.nodes, node);
-    work.x += 1;
-    float tl, tr;
-    const int m = node_hits(r, n, tmin, h.t, tl, tr);
-#pragma unroll
-    for (int side = 0; side < 2; ++side) {
-        const int child = side ? n.d.y : n.d.x;
-        const int cnt = side ? n.d.w : n.d.z;
-        if ((m & (1 << side)) && child < 0) {
-            const int first = ~child;
-            work.y += cnt;
-            for (int i = 0; i < cnt; ++i) {
-                const float4* tp = sc.tris + 3 * (first + i);
-                const float4 p0 = __ldg(tp), p1 = __ldg(tp + 1), p2 = __ldg(tp + 2);
-                const float t = tri_hit(r, p0, p1, p2, tmin, h.t);
-                const int oi = inst >= 0 ? inst : __float_as_int(p2.w);
-                if (t >= 0.0f && better_hit(t, oi, __float_as_int(p0.w), h)) {
-                    h.t = t; h.inst = oi; h.tri = first + i; h.prim = __float_as_int(p0.w); h.rec = rec;
-                }
-            }
-        }
-    }
-    const bool gl = (m & 1) && n.d.x >= 0 && tl <= h.t;
-    const bool gr = (m & 2) && n.d.y >= 0 && tr <= h.t;
-    int next = MCEV_NO_NODE;
-    if (gl && gr) {
-        const int nearc = tl <= tr ? n.d.x : n.d.y;
-        const int farc = tl <= tr ? n.d.y : n.d.x;
-        if (sp < MCEV_STACK) stack[SIDX(sp++)] = farc;
-        else *err = 1;
-        next = nearc;
-    } else if (gl) {
-        next = n.d.x;
-    } else if (gr) {
-        next = n.d.y;
-    }
-    if (next == MCEV_NO_NODE) {
-        if (sp == base) return false;
-        next = stack[SIDX(--sp)];
-    }
-    node = next;
-    return true;
-}
-
-__device__ __forceinline__ void blas_closest(const DevScene& sc, int root, int rec, int inst, const WRay& r,
-                                             float tmin, Hit& h, int* stack, int base, int* err, int3& work) {
-    int sp = base;
-    int node = root;
-    while (step_closest(sc, rec, inst, r, tmin, h, stack, base, sp, node, err, work)) {
-    }
-}
-
-// One node of an any-hit BLAS traversal.  Returns 0 to continue, 1 when
-// finished without a hit, 2 when an occluder was found.
-__device__ __forceinline__ int step_any(const DevScene& sc, const WRay& r, float tmin, float tmax, int* stack,
-                                        int base, int& sp, int& node, int* err, int3& work) {
-    const Node n = load_node(sc.nodes, node);
-    work.x += 1;
-    float tl, tr;
-    const int m = node_hits(r, n, tmin, tmax, tl, tr);
-#pragma unroll
-    for (int side = 0; side < 2; ++side) {
-        const int child = side ? n.d.y : n.d.x;
-        const int cnt = side ? n.d.w : n.d.z;
-        if ((m & (1 << side)) && child < 0) {
-            const int first = ~child;
-            for (int i = 0; i < cnt; ++i) {
-                const float4* tp = sc.tris + 3 * (first + i);
-                work.y += 1;
-                if (tri_hit(r, __ldg(tp), __ldg(tp + 1), __ldg(tp + 2), tmin, tmax) >= 0.0f) return 2;
-            }
-        }
-    }
-    const bool gl = (m & 1) && n.d.x >= 0;
-    const bool gr = (m & 2) && n.d.y >= 0;
-    int next = MCEV_NO_NODE;
-    if (gl && gr) {
-#if MCEV_ANY_ORDERED
-        const int nearc = tl <= tr ? n.d.x : n.d.y;
-        const int farc = tl <= tr ? n.d.y : n.d.x;
-#else
-        const int nearc = n.d.x;
-        const int farc = n.d.y;
-#endif
-        if (sp < MCEV_STACK) stack[SIDX(sp++)] = farc;
-        else *err = 1;
-        next = nearc;
-    } else if (gl) {
-        next = n.d.x;
-    } else if (gr) {
-        next = n.d.y;
-    }
-    if (next == MCEV_NO_NODE) {
-        if (sp == base) return 1;
-        next = stack[SIDX(--sp)];
-    }
-    node = next;
-    return 0;
-}
-
-__device__ __forceinline__ bool blas_any(const DevScene& sc, int root, const WRay& r, float tmin, float tmax,
-                                         int* stack, int base, int* err, int3& work) {
-    int sp = base;
-    int node = root;
-    while (true) {
-        const int s = step_any(sc, r, tmin, tmax, stack, base, sp, node, err, work);
-        if (s) return s == 2;
-    }
-}
-
 // ------------------------------------------------------------------ compressed 8-wide BLAS
 // Traversal of the Node8 layout (layout.h).  A "node group" is a 64-bit word
 // pair (child_base, bits): bits 24..31 mark the internal children of one node
@@ -546,27 +428,10 @@ __device__ __forceinline__ bool blas_wide(const DevScene& sc, uint32_t root, int
     // the root as the only (internal, slot 0) child of a virtual parent
     uint2 g = make_uint2(root, (1u << (24 + ox)) | 1u);
     int sp = 0;
+    // one loop iteration per node OR per triangle (as in the two-wide loop)
+    uint32_t tb = 0, tbits = 0, tmask = 0;
     while (true) {
-        uint32_t tb = 0, tbits = 0, tmask = 0;
-        if (g.y & 0xFF000000u) {
-            const uint32_t key = __ffs(g.y >> 24) - 1;
-            g.y &= ~(1u << (24 + key));
-            const uint32_t slot = key ^ ox;
-            const uint32_t child = g.x + __popc(g.y & ((1u << slot) - 1u) & 0xFFu);
-            if (g.y & 0xFF000000u) {
-                if (sp < MCEV_WSTACK) stack[sp++] = g;
-                else *err = 1;
-            }
-            uint32_t cb, im;
-            int nv;
-            const uint32_t hit8 =
-                wide_node_hits(sc.wnodes, child, r, ox, tmin, kAny ? tmax : h.t, cb, tb, im, tmask, nv);
-            work.x += 1;
-            work.z += nv;
-            g = make_uint2(cb, (xor_permute8(hit8 & im, ox) << 24) | im);
-            tbits = spread3(hit8 & ~im) & tmask;
-        }
-        while (tbits) {
+        if (tbits) {
             const uint32_t bit = (uint32_t)(__ffs(tbits) - 1);
             tbits &= tbits - 1;
             const uint32_t ti = tb + __popc(tmask & ((1u << bit) - 1u));
@@ -582,13 +447,136 @@ __device__ __forceinline__ bool blas_wide(const DevScene& sc, uint32_t root, int
                     h.t = t; h.inst = oi; h.tri = (int)ti; h.prim = __float_as_int(p0.w); h.rec = rec;
                 }
             }
+            continue;
         }
         if (!(g.y & 0xFF000000u)) {
             if (sp == 0) break;
             g = stack[--sp];
         }
+        const uint32_t key = __ffs(g.y >> 24) - 1;
+        g.y &= ~(1u << (24 + key));
+        const uint32_t slot = key ^ ox;
+        const uint32_t child = g.x + __popc(g.y & ((1u << slot) - 1u) & 0xFFu);
+        if (g.y & 0xFF000000u) {
+            if (sp < MCEV_WSTACK) stack[sp++] = g;
+            else *err = 1;
+        }
+        uint32_t cb, im;
+        int nv;
+        const uint32_t hit8 = wide_node_hits(sc.wnodes, child, r, ox, tmin, kAny ? tmax : h.t, cb, tb, im, tmask, nv);
+        work.x += 1;
+        work.z += nv;
+        g = make_uint2(cb, (xor_permute8(hit8 & im, ox) << 24) | im);
+        tbits = spread3(hit8 & ~im) & tmask;
     }
     return false;
+}
+
+// Two-wide BLAS traversal, one loop iteration per node step OR per leaf
+// triangle: a node step records its hit leaf children as a pending triangle
+// range (sibling leaves are contiguous in the leaf order) instead of testing
+// them at once, and the lane tests one pending triangle per iteration before
+// its next node step.  Lanes testing triangles and lanes stepping through
+// nodes then share warp iterations, instead of the warp running every lane's
+// triangle loop while the others wait (measured: 75 % of warp-steps of the
+// terrain frame carried such loops at 6 % lane activity).  Nodes and
+// triangles are visited in the same order as a test-at-once traversal, so
+// the closest hit is the same.
+// rec: instance record; inst: its uploaded instance id, or -1 for the merged
+// static geometry whose triangles carry their own instance id (v2.w).
+
+__device__ __forceinline__ void blas_closest(const DevScene& sc, int root, int rec, int inst, const WRay& r,
+                                                  float tmin, Hit& h, int* stack, int base, int* err, int3& work) {
+    int sp = base, node = root;
+    int pfirst = 0, pcount = 0;
+    while (true) {
+        if (pcount > 0) {
+            const float4* tp = sc.tris + 3 * pfirst;
+            const float4 p0 = __ldg(tp), p1 = __ldg(tp + 1), p2 = __ldg(tp + 2);
+            const float t = tri_hit(r, p0, p1, p2, tmin, h.t);
+            const int oi = inst >= 0 ? inst : __float_as_int(p2.w);
+            if (t >= 0.0f && better_hit(t, oi, __float_as_int(p0.w), h)) {
+                h.t = t; h.inst = oi; h.tri = pfirst; h.prim = __float_as_int(p0.w); h.rec = rec;
+            }
+            work.y += 1;
+            ++pfirst;
+            --pcount;
+            continue;
+        }
+        if (node == MCEV_NO_NODE) {
+            if (sp == base) break;
+            node = stack[SIDX(--sp)];
+        }
+        const Node n = load_node(sc.nodes, node);
+        work.x += 1;
+        float tl, tr;
+        const int m = node_hits(r, n, tmin, h.t, tl, tr);
+        const bool lh = (m & 1) && n.d.x < 0, rh = (m & 2) && n.d.y < 0;
+        pfirst = lh ? ~n.d.x : ~n.d.y;
+        pcount = (lh ? n.d.z : 0) + (rh ? n.d.w : 0);
+        const bool gl = (m & 1) && n.d.x >= 0 && tl <= h.t;
+        const bool gr = (m & 2) && n.d.y >= 0 && tr <= h.t;
+        int next = MCEV_NO_NODE;
+        if (gl && gr) {
+            const int nearc = tl <= tr ? n.d.x : n.d.y;
+            const int farc = tl <= tr ? n.d.y : n.d.x;
+            if (sp < MCEV_STACK) stack[SIDX(sp++)] = farc;
+            else *err = 1;
+            next = nearc;
+        } else if (gl) {
+            next = n.d.x;
+        } else if (gr) {
+            next = n.d.y;
+        }
+        node = next;
+    }
+}
+
+__device__ __forceinline__ bool blas_any(const DevScene& sc, int root, const WRay& r, float tmin, float tmax,
+                                              int* stack, int base, int* err, int3& work) {
+    int sp = base, node = root;
+    int pfirst = 0, pcount = 0;
+    while (true) {
+        if (pcount > 0) {
+            const float4* tp = sc.tris + 3 * pfirst;
+            work.y += 1;
+            if (tri_hit(r, __ldg(tp), __ldg(tp + 1), __ldg(tp + 2), tmin, tmax) >= 0.0f) return true;
+            ++pfirst;
+            --pcount;
+            continue;
+        }
+        if (node == MCEV_NO_NODE) {
+            if (sp == base) return false;
+            node = stack[SIDX(--sp)];
+        }
+        const Node n = load_node(sc.nodes, node);
+        work.x += 1;
+        float tl, tr;
+        const int m = node_hits(r, n, tmin, tmax, tl, tr);
+        const bool lh = (m & 1) && n.d.x < 0, rh = (m & 2) && n.d.y < 0;
+        pfirst = lh ? ~n.d.x : ~n.d.y;
+        pcount = (lh ? n.d.z : 0) + (rh ? n.d.w : 0);
+        const bool gl = (m & 1) && n.d.x >= 0;
+        const bool gr = (m & 2) && n.d.y >= 0;
+        int next = MCEV_NO_NODE;
+        if (gl && gr) {
+#if MCEV_ANY_ORDERED
+            const int nearc = tl <= tr ? n.d.x : n.d.y;
+            const int farc = tl <= tr ? n.d.y : n.d.x;
+#else
+            const int nearc = n.d.x;
+            const int farc = n.d.y;
+#endif
+            if (sp < MCEV_STACK) stack[SIDX(sp++)] = farc;
+            else *err = 1;
+            next = nearc;
+        } else if (gl) {
+            next = n.d.x;
+        } else if (gr) {
+            next = n.d.y;
+        }
+        node = next;
+    }
 }
 
 // instance record: rows M0..M2, Minv0..Minv2, (root, override, instance id, 0)
