@@ -21,13 +21,14 @@
 
 namespace mcev {
 
-// Minimum resident blocks per SM requested for the traversal kernels: 8
-// blocks of 128 threads caps them at 64 registers (50% occupancy), which hides
-// more node-fetch latency than the 80-register build (measured 11% faster on
-// the 1280x720 terrain frame; 10 or 12 blocks spill and lose).  0 leaves the
+// Minimum resident blocks per SM requested for the traversal kernels: 9
+// blocks of 128 threads cap them at 56 registers (56% occupancy); traversal
+// waits on node fetches, so more resident warps pay more than the few
+// registers spilled (terrain frame traversal: 72 registers 1011 ms, 64
+// registers 967 ms, 56 registers 943 ms, 48 registers 961 ms).  0 leaves the
 // choice to the compiler.
 #ifndef MCEV_TRAV_MINB
-#define MCEV_TRAV_MINB 8
+#define MCEV_TRAV_MINB 9
 #endif
 // The wide-node traversal keeps a whole node (five 16-byte words) and its
 // eight child tests in flight: it gets its own cap.
