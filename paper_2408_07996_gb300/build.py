@@ -17,6 +17,13 @@ LIB = os.path.join(OUT, "libmcev.so")
 SOURCES = ["kernels.cu", "quality.cu", "api.cpp", "bvh.cpp", "bvh8.cpp", "tdist.cpp"]
 HEADERS = ["layout.h", "device.cuh", "kernels.h", "quality.h", "bvh.h", "tdist.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# kernels.cu is compiled without implicit multiply-add contraction: its
+# traversal code is instantiated several times (single frame or batched jobs,
+# two BVH layouts, different register caps), and the compiler may fuse a
+# different product of the same expression in each, so the same ray could
+# round differently in two instantiations.  The fused multiply-adds that the
+# hot loops want are written out as fmaf().
+PER_SOURCE = {"kernels.cu": ["-fmad=false"]}
 
 
 def nvcc() -> str:
@@ -43,7 +50,7 @@ def build(force: bool = False, verbose: bool = False, extra: list | None = None)
     procs, objs = [], []
     for src in SOURCES:
         obj = os.path.join(OUT, os.path.splitext(src)[0] + ".o")
-        cmd = [cc, *common, *(extra or [])]
+        cmd = [cc, *common, *PER_SOURCE.get(src, []), *(extra or [])]
         if src.endswith(".cu"):
             cmd += [*ARCH, "-lineinfo", "-Xptxas", "-v" if verbose else "-O3"]
         cmd += ["-c", os.path.join(CSRC, src), "-o", obj]

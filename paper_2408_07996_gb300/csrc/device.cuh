@@ -40,26 +40,26 @@ __device__ __forceinline__ f3 mk3(float x, float y, float z) { return f3{x, y, z
 __device__ __forceinline__ f3 operator+(f3 a, f3 b) { return mk3(a.x + b.x, a.y + b.y, a.z + b.z); }
 __device__ __forceinline__ f3 operator-(f3 a, f3 b) { return mk3(a.x - b.x, a.y - b.y, a.z - b.z); }
 __device__ __forceinline__ f3 operator*(f3 a, float s) { return mk3(a.x * s, a.y * s, a.z * s); }
-__device__ __forceinline__ float dot3(f3 a, f3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float dot3(f3 a, f3 b) { return fmaf(a.z, b.z, fmaf(a.y, b.y, a.x * b.x)); }
 __device__ __forceinline__ f3 cross3(f3 a, f3 b) {
-    return mk3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+    return mk3(fmaf(a.y, b.z, -(a.z * b.y)), fmaf(a.z, b.x, -(a.x * b.z)), fmaf(a.x, b.y, -(a.y * b.x)));
 }
 __device__ __forceinline__ f3 norm3(f3 a) { return a * (1.0f / sqrtf(dot3(a, a))); }
 __device__ __forceinline__ f3 xyz(float4 v) { return mk3(v.x, v.y, v.z); }
 
 // row-major 3x4 affine (rows r0, r1, r2)
 __device__ __forceinline__ f3 xf_point(float4 r0, float4 r1, float4 r2, f3 p) {
-    return mk3(r0.x * p.x + r0.y * p.y + r0.z * p.z + r0.w, r1.x * p.x + r1.y * p.y + r1.z * p.z + r1.w,
-               r2.x * p.x + r2.y * p.y + r2.z * p.z + r2.w);
+    return mk3(fmaf(r0.z, p.z, fmaf(r0.y, p.y, fmaf(r0.x, p.x, r0.w))),
+               fmaf(r1.z, p.z, fmaf(r1.y, p.y, fmaf(r1.x, p.x, r1.w))),
+               fmaf(r2.z, p.z, fmaf(r2.y, p.y, fmaf(r2.x, p.x, r2.w))));
 }
 __device__ __forceinline__ f3 xf_vec(float4 r0, float4 r1, float4 r2, f3 p) {
-    return mk3(r0.x * p.x + r0.y * p.y + r0.z * p.z, r1.x * p.x + r1.y * p.y + r1.z * p.z,
-               r2.x * p.x + r2.y * p.y + r2.z * p.z);
+    return mk3(dot3(xyz(r0), p), dot3(xyz(r1), p), dot3(xyz(r2), p));
 }
 // (A^-1)^T n from the rows of the inverse
 __device__ __forceinline__ f3 xf_normal(float4 i0, float4 i1, float4 i2, f3 n) {
-    return mk3(i0.x * n.x + i1.x * n.y + i2.x * n.z, i0.y * n.x + i1.y * n.y + i2.y * n.z,
-               i0.z * n.x + i1.z * n.y + i2.z * n.z);
+    return mk3(fmaf(i2.x, n.z, fmaf(i1.x, n.y, i0.x * n.x)), fmaf(i2.y, n.z, fmaf(i1.y, n.y, i0.y * n.x)),
+               fmaf(i2.z, n.z, fmaf(i1.z, n.y, i0.z * n.x)));
 }
 
 // ------------------------------------------------------------------ Philox4x32-10
@@ -266,13 +266,13 @@ __device__ __forceinline__ float tri_hit(const WRay& r, float4 p0, float4 p1, fl
     const float Ax = dot3(r.mx, A), Ay = dot3(r.my, A);
     const float Bx = dot3(r.mx, B), By = dot3(r.my, B);
     const float Cx = dot3(r.mx, C), Cy = dot3(r.my, C);
-    const float U = Cx * By - Cy * Bx;
-    const float V = Ax * Cy - Ay * Cx;
-    const float W = Bx * Ay - By * Ax;
+    const float U = fmaf(Cx, By, -(Cy * Bx));
+    const float V = fmaf(Ax, Cy, -(Ay * Cx));
+    const float W = fmaf(Bx, Ay, -(By * Ax));
     if ((U < 0.0f || V < 0.0f || W < 0.0f) && (U > 0.0f || V > 0.0f || W > 0.0f)) return -1.0f;
     const float det = U + V + W;
     if (det == 0.0f) return -1.0f;
-    const float T = U * dot3(r.mz, A) + V * dot3(r.mz, B) + W * dot3(r.mz, C);
+    const float T = fmaf(W, dot3(r.mz, C), fmaf(V, dot3(r.mz, B), U * dot3(r.mz, A)));
     const float t = T / det;
     return (t > tmin && t <= tmax) ? t : -1.0f;
 }
@@ -292,12 +292,12 @@ __device__ __forceinline__ float max3f(float a, float b, float c) {
 // slab test of both children of a node; returns hit mask (bit0 left, bit1 right)
 __device__ __forceinline__ int node_hits(const WRay& r, const Node& n, float tmin, float tmax, float& tl, float& tr) {
     const float4 a = n.a, b = n.b, c = n.c;
-    const float lx0 = a.x * r.idir.x - r.oidir.x, lx1 = a.y * r.idir.x - r.oidir.x;
-    const float ly0 = a.z * r.idir.y - r.oidir.y, ly1 = a.w * r.idir.y - r.oidir.y;
-    const float lz0 = c.x * r.idir.z - r.oidir.z, lz1 = c.y * r.idir.z - r.oidir.z;
-    const float rx0 = b.x * r.idir.x - r.oidir.x, rx1 = b.y * r.idir.x - r.oidir.x;
-    const float ry0 = b.z * r.idir.y - r.oidir.y, ry1 = b.w * r.idir.y - r.oidir.y;
-    const float rz0 = c.z * r.idir.z - r.oidir.z, rz1 = c.w * r.idir.z - r.oidir.z;
+    const float lx0 = fmaf(a.x, r.idir.x, -r.oidir.x), lx1 = fmaf(a.y, r.idir.x, -r.oidir.x);
+    const float ly0 = fmaf(a.z, r.idir.y, -r.oidir.y), ly1 = fmaf(a.w, r.idir.y, -r.oidir.y);
+    const float lz0 = fmaf(c.x, r.idir.z, -r.oidir.z), lz1 = fmaf(c.y, r.idir.z, -r.oidir.z);
+    const float rx0 = fmaf(b.x, r.idir.x, -r.oidir.x), rx1 = fmaf(b.y, r.idir.x, -r.oidir.x);
+    const float ry0 = fmaf(b.z, r.idir.y, -r.oidir.y), ry1 = fmaf(b.w, r.idir.y, -r.oidir.y);
+    const float rz0 = fmaf(c.z, r.idir.z, -r.oidir.z), rz1 = fmaf(c.w, r.idir.z, -r.oidir.z);
     const float ln = max3f(fminf(lx0, lx1), fminf(ly0, ly1), fmaxf(fminf(lz0, lz1), tmin));
     const float lf = min3f(fmaxf(lx0, lx1), fmaxf(ly0, ly1), fminf(fmaxf(lz0, lz1), tmax));
     const float rn = max3f(fminf(rx0, rx1), fminf(ry0, ry1), fmaxf(fminf(rz0, rz1), tmin));
