@@ -332,7 +332,7 @@ QUALITY_BYTES_PER_EVENT = 4
 # one-pass ncu capture of every launch of one timed terrain frame (326.5 GB
 # over 294 launches that traced 3.852 G closest-hit and shadow rays); set to
 # None when the traversal kernels change.
-TRAVERSAL_DRAM_BYTES_PER_RAY = 84.77
+TRAVERSAL_DRAM_BYTES_PER_RAY = None
 
 
 def traversal_traffic(rays_per_launch: float, bvh_width: int = 2):

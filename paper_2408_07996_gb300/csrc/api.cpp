@@ -594,10 +594,13 @@ mcev_status frame_setup(mcev_ctx* ctx, double t, int slot) {
         std::memcpy(&tail.z, &oid, 4);
         inst[7 * r + 6] = tail;
     }
-    // TLAS over instance records, one record per leaf; leaf ref = ~record
+    // TLAS over the moving instances' records, one record per leaf; leaf
+    // ref = ~record.  The merged static geometry (last record) stays out of
+    // it: it spans the scene, and rays traverse it first.
+    const int n_tlas = nr - (ctx->has_static ? 1 : 0);
     std::vector<Node> tlas;
-    if (nr > 1) {
-        BuiltBvh b = build_bvh(blo.data(), bhi.data(), bce.data(), nr, 16, 1);
+    if (n_tlas > 1) {
+        BuiltBvh b = build_bvh(blo.data(), bhi.data(), bce.data(), n_tlas, 16, 1);
         tlas = b.nodes;
         for (Node& nd : tlas) {
             if (nd.d.x < 0 && nd.d.z > 0) nd.d.x = ~b.order[~nd.d.x];
@@ -655,7 +658,8 @@ mcev_status frame_setup(mcev_ctx* ctx, double t, int slot) {
     d.lights = (const float4*)(base + al(nb_t) + al(nb_i));
     d.n_inst = nr;
     d.n_lights = (int32_t)ctx->emitters.size();
-    d.tlas_is_leaf = nr <= 1 ? 1 : 0;
+    d.n_tlas = n_tlas;
+    d.static_rec = ctx->has_static ? n_tlas : -1;
     // camera (FP64 then rounded)
     double eye[3], tgt[3], up[3];
     for (int a = 0; a < 3; ++a) {

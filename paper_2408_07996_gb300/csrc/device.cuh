@@ -616,8 +616,9 @@ __device__ __forceinline__ bool blas_any_layout(const DevScene& sc, int root, co
 #define MCEV_DECLARE_WSTACK(name) uint2 name[kWide ? MCEV_WSTACK : 1]
 
 // world-space closest hit over the two-level hierarchy (the TLAS is two-wide;
-// BLAS in the scene's layout).  work: (node fetches, triangle tests, box
-// tests of the wide layout)
+// BLAS in the scene's layout): the merged never-moving geometry first, then
+// the TLAS of the moving instances, whose boxes the hit found so far culls.
+// work: (node fetches, triangle tests, box tests of the wide layout)
 template <bool kWide>
 __device__ __forceinline__ Hit closest_hit(const DevScene& sc, const DevFrame& fr, f3 o, f3 d, float tmin, int* err,
                                            int3& work) {
@@ -629,8 +630,13 @@ __device__ __forceinline__ Hit closest_hit(const DevScene& sc, const DevFrame& f
     h.rec = -1;
     MCEV_DECLARE_STACK(stack);
     MCEV_DECLARE_WSTACK(wstack);
-    if (fr.n_inst == 0) return h;
-    if (fr.tlas_is_leaf) {
+    if (fr.static_rec >= 0) {
+        int root, oi;
+        const WRay r = object_ray(fr, fr.static_rec, o, d, root, oi);
+        blas_closest_any_layout<kWide>(sc, root, fr.static_rec, oi, r, tmin, h, stack, 0, wstack, err, work);
+    }
+    if (fr.n_tlas == 0) return h;
+    if (fr.n_tlas == 1) {
         int root, oi;
         const WRay r = object_ray(fr, 0, o, d, root, oi);
         blas_closest_any_layout<kWide>(sc, root, 0, oi, r, tmin, h, stack, 0, wstack, err, work);
@@ -685,8 +691,13 @@ __device__ __forceinline__ bool occluded(const DevScene& sc, const DevFrame& fr,
                                          int* err, int3& work) {
     MCEV_DECLARE_STACK(stack);
     MCEV_DECLARE_WSTACK(wstack);
-    if (fr.n_inst == 0) return false;
-    if (fr.tlas_is_leaf) {
+    if (fr.static_rec >= 0) {
+        int root, oi;
+        const WRay r = object_ray(fr, fr.static_rec, o, d, root, oi);
+        if (blas_any_layout<kWide>(sc, root, r, tmin, tmax, stack, 0, wstack, err, work)) return true;
+    }
+    if (fr.n_tlas == 0) return false;
+    if (fr.n_tlas == 1) {
         int root, oi;
         const WRay r = object_ray(fr, 0, o, d, root, oi);
         return blas_any_layout<kWide>(sc, root, r, tmin, tmax, stack, 0, wstack, err, work);

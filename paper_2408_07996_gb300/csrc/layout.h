@@ -102,8 +102,12 @@ struct DevFrame {
     const float4* inst;       // 7 float4 per instance
     const float4* lights;     // 4 float4 per emissive triangle
     int32_t n_inst, n_lights;
-    int32_t tlas_is_leaf;     // TLAS has a single instance: no TLAS traversal needed
-    int32_t pad0;
+    // records 0 .. n_tlas-1 (the moving instances) sit under the TLAS; with
+    // n_tlas == 1 there is nothing to traverse.  The merged never-moving
+    // geometry, if any, is record static_rec (= n_tlas) and is traversed on
+    // its own, before the TLAS.
+    int32_t n_tlas;
+    int32_t static_rec;       // or -1
     float eye[3], fwd[3], right[3], up[3];  // right, up prescaled by tan(fov/2)*aspect
     uint32_t key0, key1;      // Philox key
     float p_env, p_area;      // NEE light-type selection probabilities
