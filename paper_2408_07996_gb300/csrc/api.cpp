@@ -829,6 +829,7 @@ struct BatchRun {
     int32_t max_depth = 0;
     bool any_nee = false;
     bool wide = false;        // every job's BLAS use the wide layout
+    bool any_tlas = false;    // some job's frame has two or more moving instances
 };
 
 // one chunk of n_paths = nj * spp_r paths through every bounce (with rc:
@@ -843,12 +844,14 @@ mcev_status trace_chunk(mcev_ctx* ctx, const Frame& fr, const DevParams& P, cons
     const int depth_max = B ? B->max_depth : P.max_depth;
     const bool nee = B ? B->any_nee : P.nee != 0;
     const bool wide = B ? B->wide : ctx->dsc.wide != 0;
+    const bool tlas = B ? B->any_tlas : fr.dev.n_tlas >= 2;
+    const int trav = (wide ? TRAV_WIDE : 0) | (tlas ? TRAV_TLAS : 0);
     NvtxRange range("mcev chunk");
     LAUNCH(MCEV_K_RAYGEN,
            launch_raygen(fr.dev, P, w, queue, j0, spp_r, k_base, n_paths, 0, ctx->sms, ctx->stream, jobs, rc));
     int cur = 0;
     LAUNCH(MCEV_K_EXTEND,
-           launch_extend(ctx->dsc, fr.dev, P.t_min, w, cur, n_paths, err, ctx->sms, ctx->stream, jobs, wide));
+           launch_extend(ctx->dsc, fr.dev, P.t_min, w, cur, n_paths, err, ctx->sms, ctx->stream, jobs, trav));
     for (int depth = 0; depth <= depth_max; ++depth) {
         LAUNCH(MCEV_K_SHADE, launch_shade(ctx->dsc, fr.dev, P, w, cur, n_paths, ctx->sms, ctx->stream, jobs));
         if (depth < depth_max) {
@@ -856,16 +859,16 @@ mcev_status trace_chunk(mcev_ctx* ctx, const Frame& fr, const DevParams& P, cons
             // this bounce's shadow rays and the next bounce's closest hits in one launch
             if (nee)
                 LAUNCH(MCEV_K_EXTEND, launch_shadow_extend(ctx->dsc, fr.dev, P, w, cur, n_paths, err, ctx->sms,
-                                                           ctx->stream, jobs, wide));
+                                                           ctx->stream, jobs, trav));
             else
                 LAUNCH(MCEV_K_EXTEND, launch_extend(ctx->dsc, fr.dev, P.t_min, w, cur ^ 1, n_paths, err, ctx->sms,
-                                                    ctx->stream, jobs, wide));
+                                                    ctx->stream, jobs, trav));
 #else
             if (nee)
                 LAUNCH(MCEV_K_SHADOW, launch_shadow(ctx->dsc, fr.dev, P, w, cur, n_paths, err, ctx->sms, ctx->stream,
-                                                    jobs, wide));
+                                                    jobs, trav));
             LAUNCH(MCEV_K_EXTEND, launch_extend(ctx->dsc, fr.dev, P.t_min, w, cur ^ 1, n_paths, err, ctx->sms,
-                                                ctx->stream, jobs, wide));
+                                                ctx->stream, jobs, trav));
 #endif
         }
         cur ^= 1;
@@ -1606,6 +1609,7 @@ mcev_status mcev_render_events_batch(mcev_ctx* runner, const mcev_job* jobs, int
         B.q0 = 0;
         B.max_depth = 0;
         B.any_nee = false;
+        B.any_tlas = false;
         for (size_t q = 0; q < list.size(); ++q) {
             mcev_ctx* c = jobs[list[q]].ctx;
             Job& J = tab[q];
@@ -1620,6 +1624,7 @@ mcev_status mcev_render_events_batch(mcev_ctx* runner, const mcev_job* jobs, int
             J.mean_out = jobs[list[q]].mean_out;
             B.max_depth = std::max(B.max_depth, c->params.max_depth);
             B.any_nee = B.any_nee || c->params.nee != 0;
+            B.any_tlas = B.any_tlas || J.fr.n_tlas >= 2;
             const int64_t np = (int64_t)c->W * c->H;
             LAUNCH(MCEV_K_STATS, launch_fill_entries(B.queue[0] + B.q0, np, (int)q, ctx->sms, ctx->stream));
             B.q0 += np;

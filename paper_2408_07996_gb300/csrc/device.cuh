@@ -615,11 +615,115 @@ __device__ __forceinline__ bool blas_any_layout(const DevScene& sc, int root, co
 
 #define MCEV_DECLARE_WSTACK(name) uint2 name[kWide ? MCEV_WSTACK : 1]
 
+// The slab-test part of make_wray (reciprocal direction and origin times it),
+// enough for TLAS box tests; the same arithmetic as make_wray.
+__device__ __forceinline__ void slab_ray(WRay& r, f3 o, f3 d) {
+    const float ooeps = 0x1p-80f;
+    r.idir = mk3(1.0f / (fabsf(d.x) > ooeps ? d.x : copysignf(ooeps, d.x)),
+                 1.0f / (fabsf(d.y) > ooeps ? d.y : copysignf(ooeps, d.y)),
+                 1.0f / (fabsf(d.z) > ooeps ? d.z : copysignf(ooeps, d.z)));
+    r.oidir = mk3(o.x * r.idir.x, o.y * r.idir.y, o.z * r.idir.z);
+}
+
+// Two-level traversal of the moving instances (TLAS, then each hit
+// instance's two-wide BLAS) as ONE loop: an iteration is a TLAS node step, a
+// BLAS node step or one pending leaf triangle, whatever the lane is at, so
+// lanes that entered different instances at different TLAS steps still
+// advance together (with the BLAS loop nested in the TLAS loop, a warp ran
+// the BLAS loop once for every group of lanes that reached a TLAS leaf
+// together).  A TLAS step records its hit leaf children (one instance record
+// each) as pending; they are entered before the next TLAS step, the TLAS node
+// in hand waiting on the stack.  BLAS nodes are stacked above `base`, the
+// TLAS stack height when the instance was entered.  kAny: any hit in
+// (tmin, tmax]; else closest hit into h.  Returns whether an occluder was found
+// (kAny).
+template <bool kAny>
+__device__ __forceinline__ bool two_level(const DevScene& sc, const DevFrame& fr, f3 o, f3 d, float tmin,
+                                          float tmax, Hit& h, int* stack, int* err, int3& work) {
+    WRay r;
+    slab_ray(r, o, d);
+    bool in_blas = false;
+    int sp = 0, base = 0, node = 0;
+    int pfirst = 0, pcount = 0;
+    int pend0 = -1, pend1 = -1;
+    int rec = -1, inst = -1;
+    while (true) {
+        if (pcount > 0) {
+            const float4* tp = sc.tris + 3 * pfirst;
+            const float4 p0 = __ldg(tp), p1 = __ldg(tp + 1), p2 = __ldg(tp + 2);
+            work.y += 1;
+            const float t = tri_hit(r, p0, p1, p2, tmin, kAny ? tmax : h.t);
+            if (kAny) {
+                if (t >= 0.0f) return true;
+            } else {
+                const int oi = inst >= 0 ? inst : __float_as_int(p2.w);
+                if (t >= 0.0f && better_hit(t, oi, __float_as_int(p0.w), h)) {
+                    h.t = t; h.inst = oi; h.tri = pfirst; h.prim = __float_as_int(p0.w); h.rec = rec;
+                }
+            }
+            ++pfirst;
+            --pcount;
+            continue;
+        }
+        if (!in_blas && pend0 >= 0) {
+            if (node != MCEV_NO_NODE) {
+                if (sp < MCEV_STACK) stack[SIDX(sp++)] = node;
+                else *err = 1;
+            }
+            rec = pend0;
+            pend0 = pend1;
+            pend1 = -1;
+            r = object_ray(fr, rec, o, d, node, inst);
+            in_blas = true;
+            base = sp;
+        }
+        if (node == MCEV_NO_NODE) {
+            if (in_blas && sp == base) {
+                // instance done: back to the TLAS
+                in_blas = false;
+                slab_ray(r, o, d);
+                if (pend0 >= 0) continue;
+            }
+            if (sp == 0) break;
+            node = stack[SIDX(--sp)];
+        }
+        const Node n = load_node(in_blas ? sc.nodes : fr.tlas, node);
+        work.x += 1;
+        float tl, tr;
+        const float tcut = kAny ? tmax : h.t;
+        const int m = node_hits(r, n, tmin, tcut, tl, tr);
+        const bool lh = (m & 1) && n.d.x < 0, rh = (m & 2) && n.d.y < 0;
+        if (in_blas) {
+            pfirst = lh ? ~n.d.x : ~n.d.y;
+            pcount = (lh ? n.d.z : 0) + (rh ? n.d.w : 0);
+        } else {
+            pend0 = lh ? ~n.d.x : (rh ? ~n.d.y : -1);
+            pend1 = (lh && rh) ? ~n.d.y : -1;
+        }
+        const bool gl = (m & 1) && n.d.x >= 0 && (kAny || tl <= h.t);
+        const bool gr = (m & 2) && n.d.y >= 0 && (kAny || tr <= h.t);
+        int next = MCEV_NO_NODE;
+        if (gl && gr) {
+            // nearer child first (any-hit: in BLAS only, as blas_any does)
+            const bool lfirst = kAny ? (!(MCEV_ANY_ORDERED && in_blas) || tl <= tr) : tl <= tr;
+            if (sp < MCEV_STACK) stack[SIDX(sp++)] = lfirst ? n.d.y : n.d.x;
+            else *err = 1;
+            next = lfirst ? n.d.x : n.d.y;
+        } else if (gl) {
+            next = n.d.x;
+        } else if (gr) {
+            next = n.d.y;
+        }
+        node = next;
+    }
+    return false;
+}
+
 // world-space closest hit over the two-level hierarchy (the TLAS is two-wide;
 // BLAS in the scene's layout): the merged never-moving geometry first, then
 // the TLAS of the moving instances, whose boxes the hit found so far culls.
 // work: (node fetches, triangle tests, box tests of the wide layout)
-template <bool kWide>
+template <bool kWide, bool kTlas>
 __device__ __forceinline__ Hit closest_hit(const DevScene& sc, const DevFrame& fr, f3 o, f3 d, float tmin, int* err,
                                            int3& work) {
     Hit h;
@@ -636,12 +740,18 @@ __device__ __forceinline__ Hit closest_hit(const DevScene& sc, const DevFrame& f
         blas_closest_any_layout<kWide>(sc, root, fr.static_rec, oi, r, tmin, h, stack, 0, wstack, err, work);
     }
     if (fr.n_tlas == 0) return h;
-    if (fr.n_tlas == 1) {
+    if (!kTlas || fr.n_tlas == 1) {
+        // (kTlas = false is launched only for frames with at most one moving instance)
         int root, oi;
         const WRay r = object_ray(fr, 0, o, d, root, oi);
         blas_closest_any_layout<kWide>(sc, root, 0, oi, r, tmin, h, stack, 0, wstack, err, work);
         return h;
     }
+    if (!kWide) {
+        two_level<false>(sc, fr, o, d, tmin, 0.0f, h, stack, err, work);
+        return h;
+    }
+    // wide BLAS: the TLAS loop with each instance's traversal nested in it
     const WRay wr = make_wray(o, d);
     int sp = 0;
     int node = 0;
@@ -686,7 +796,7 @@ __device__ __forceinline__ Hit closest_hit(const DevScene& sc, const DevFrame& f
     return h;
 }
 
-template <bool kWide>
+template <bool kWide, bool kTlas>
 __device__ __forceinline__ bool occluded(const DevScene& sc, const DevFrame& fr, f3 o, f3 d, float tmin, float tmax,
                                          int* err, int3& work) {
     MCEV_DECLARE_STACK(stack);
@@ -697,10 +807,14 @@ __device__ __forceinline__ bool occluded(const DevScene& sc, const DevFrame& fr,
         if (blas_any_layout<kWide>(sc, root, r, tmin, tmax, stack, 0, wstack, err, work)) return true;
     }
     if (fr.n_tlas == 0) return false;
-    if (fr.n_tlas == 1) {
+    if (!kTlas || fr.n_tlas == 1) {
         int root, oi;
         const WRay r = object_ray(fr, 0, o, d, root, oi);
         return blas_any_layout<kWide>(sc, root, r, tmin, tmax, stack, 0, wstack, err, work);
+    }
+    if (!kWide) {
+        Hit dummy;
+        return two_level<true>(sc, fr, o, d, tmin, tmax, dummy, stack, err, work);
     }
     const WRay wr = make_wray(o, d);
     int sp = 0;

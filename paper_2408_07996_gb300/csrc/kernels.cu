@@ -121,7 +121,7 @@ __device__ __forceinline__ void add_work(const Wave& w, int which, int3 work) {
 // Closest hits of the rays of queue `cur`, indices first, first + stride, ...
 // The first thread also clears the queue and shadow counters shade(cur) will
 // append to.
-template <bool kBatch, bool kWide>
+template <bool kBatch, bool kWide, bool kTlas>
 __device__ __forceinline__ void extend_rays(const DevScene& sc, const DevFrame& fr, float t_min, const Wave& w,
                                             int cur, int32_t* err, const Job* __restrict__ jobs, int64_t first,
                                             int64_t stride) {
@@ -140,17 +140,17 @@ __device__ __forceinline__ void extend_rays(const DevScene& sc, const DevFrame& 
         const DevScene& S = kBatch ? jobs[job].sc : sc;
         const DevFrame& F = kBatch ? jobs[job].fr : fr;
         const float tmin = kBatch ? jobs[job].P.t_min : t_min;
-        const Hit h = closest_hit<kWide>(S, F, xyz(o), xyz(d), tmin, &e, work);
+        const Hit h = closest_hit<kWide, kTlas>(S, F, xyz(o), xyz(d), tmin, &e, work);
         w.hit[i] = make_float4(h.t, __int_as_float(h.inst), __int_as_float(h.tri), __int_as_float(h.rec));
     }
     if (e) atomicOr(err, 1);
     add_work<kWide>(w, WORK_CLOSEST, work);
 }
 
-template <bool kBatch, bool kWide>
+template <bool kBatch, bool kWide, bool kTlas>
 __global__ void MCEV_TRAV_BOUNDS k_extend(DevScene sc, DevFrame fr, float t_min, Wave w, int cur, int32_t* err,
                                           const Job* __restrict__ jobs) {
-    extend_rays<kBatch, kWide>(sc, fr, t_min, w, cur, err, jobs, blockIdx.x * (int64_t)blockDim.x + threadIdx.x,
+    extend_rays<kBatch, kWide, kTlas>(sc, fr, t_min, w, cur, err, jobs, blockIdx.x * (int64_t)blockDim.x + threadIdx.x,
                                (int64_t)gridDim.x * blockDim.x);
 }
 
@@ -386,7 +386,7 @@ __device__ __forceinline__ void shadow_unoccluded(const Wave& w, const DevParams
 }
 
 // Shadow rays appended by shade(cur), indices first, first + stride, ...
-template <bool kBatch, bool kWide>
+template <bool kBatch, bool kWide, bool kTlas>
 __device__ __forceinline__ void shadow_rays(const DevScene& sc, const DevFrame& fr, const DevParams& P,
                                             const Wave& w, int cur, int32_t* err, const Job* __restrict__ jobs,
                                             int64_t first, int64_t stride) {
@@ -402,16 +402,16 @@ __device__ __forceinline__ void shadow_rays(const DevScene& sc, const DevFrame& 
         const DevScene& S = kBatch ? jobs[job].sc : sc;
         const DevFrame& F = kBatch ? jobs[job].fr : fr;
         const DevParams& Q = kBatch ? jobs[job].P : P;
-        if (!occluded<kWide>(S, F, xyz(o), xyz(d), Q.t_min, d.w, &e, work)) shadow_unoccluded(w, Q, (int)i, p);
+        if (!occluded<kWide, kTlas>(S, F, xyz(o), xyz(d), Q.t_min, d.w, &e, work)) shadow_unoccluded(w, Q, (int)i, p);
     }
     if (e) atomicOr(err, 1);
     add_work<kWide>(w, WORK_SHADOW, work);
 }
 
-template <bool kBatch, bool kWide>
+template <bool kBatch, bool kWide, bool kTlas>
 __global__ void MCEV_TRAV_BOUNDS k_shadow(DevScene sc, DevFrame fr, DevParams P, Wave w, int cur, int32_t* err,
                                           const Job* __restrict__ jobs) {
-    shadow_rays<kBatch, kWide>(sc, fr, P, w, cur, err, jobs, blockIdx.x * (int64_t)blockDim.x + threadIdx.x,
+    shadow_rays<kBatch, kWide, kTlas>(sc, fr, P, w, cur, err, jobs, blockIdx.x * (int64_t)blockDim.x + threadIdx.x,
                                (int64_t)gridDim.x * blockDim.x);
 }
 
@@ -419,14 +419,14 @@ __global__ void MCEV_TRAV_BOUNDS k_shadow(DevScene sc, DevFrame fr, DevParams P,
 // `cur`) and the closest hits of bounce d + 1 (queue 1 - cur): the first
 // `g_ext` blocks extend, the rest trace shadow rays.  Two independent traversal
 // workloads in one grid keep the SMs busy while the other's longest rays finish.
-template <bool kBatch, bool kWide>
+template <bool kBatch, bool kWide, bool kTlas>
 __global__ void MCEV_TRAV_BOUNDS k_shadow_extend(DevScene sc, DevFrame fr, DevParams P, Wave w, int cur,
                                                  int32_t g_ext, int32_t* err, const Job* __restrict__ jobs) {
     if ((int32_t)blockIdx.x < g_ext)
-        extend_rays<kBatch, kWide>(sc, fr, P.t_min, w, 1 - cur, err, jobs,
+        extend_rays<kBatch, kWide, kTlas>(sc, fr, P.t_min, w, 1 - cur, err, jobs,
                                    blockIdx.x * (int64_t)blockDim.x + threadIdx.x, (int64_t)g_ext * blockDim.x);
     else
-        shadow_rays<kBatch, kWide>(sc, fr, P, w, cur, err, jobs,
+        shadow_rays<kBatch, kWide, kTlas>(sc, fr, P, w, cur, err, jobs,
                                    (blockIdx.x - g_ext) * (int64_t)blockDim.x + threadIdx.x,
                                    (int64_t)(gridDim.x - g_ext) * blockDim.x);
 }
@@ -656,16 +656,25 @@ cudaError_t launch_raygen(const DevFrame& fr, const DevParams& P, const Wave& w,
 }
 
 // traversal launches: kBatch x kWide instantiations picked at run time
-#define MCEV_TRAV_DISPATCH(kernel, grid, ...)                                                              \
-    do {                                                                                                   \
-        if (jobs && wide) kernel<true, true><<<grid, MCEV_TRAV_BLOCK, 0, st>>>(__VA_ARGS__, jobs);          \
-        else if (jobs) kernel<true, false><<<grid, MCEV_TRAV_BLOCK, 0, st>>>(__VA_ARGS__, jobs);            \
-        else if (wide) kernel<false, true><<<grid, MCEV_TRAV_BLOCK, 0, st>>>(__VA_ARGS__, nullptr);         \
-        else kernel<false, false><<<grid, MCEV_TRAV_BLOCK, 0, st>>>(__VA_ARGS__, nullptr);                  \
+// traversal kernels by (batched jobs, BLAS layout, moving instances under a TLAS)
+#define MCEV_TRAV_LAUNCH3(kernel, kb, grid, jobs_, ...)                                                   \
+    do {                                                                                                  \
+        if (trav & TRAV_WIDE) {                                                                           \
+            if (trav & TRAV_TLAS) kernel<kb, true, true><<<grid, MCEV_TRAV_BLOCK, 0, st>>>(__VA_ARGS__, jobs_); \
+            else kernel<kb, true, false><<<grid, MCEV_TRAV_BLOCK, 0, st>>>(__VA_ARGS__, jobs_);          \
+        } else {                                                                                          \
+            if (trav & TRAV_TLAS) kernel<kb, false, true><<<grid, MCEV_TRAV_BLOCK, 0, st>>>(__VA_ARGS__, jobs_); \
+            else kernel<kb, false, false><<<grid, MCEV_TRAV_BLOCK, 0, st>>>(__VA_ARGS__, jobs_);         \
+        }                                                                                                 \
+    } while (0)
+#define MCEV_TRAV_DISPATCH(kernel, grid, ...)                                                             \
+    do {                                                                                                  \
+        if (jobs) MCEV_TRAV_LAUNCH3(kernel, true, grid, jobs, __VA_ARGS__);                               \
+        else MCEV_TRAV_LAUNCH3(kernel, false, grid, nullptr, __VA_ARGS__);                                \
     } while (0)
 
 cudaError_t launch_extend(const DevScene& sc, const DevFrame& fr, float t_min, const Wave& w, int cur, int64_t max_n,
-                          int32_t* err, int sms, cudaStream_t st, const Job* jobs, bool wide) {
+                          int32_t* err, int sms, cudaStream_t st, const Job* jobs, int trav) {
     MCEV_TRAV_DISPATCH(k_extend, grid_for(max_n, MCEV_TRAV_BLOCK, sms, 16), sc, fr, t_min, w, cur, err);
     return cudaGetLastError();
 }
@@ -680,13 +689,13 @@ cudaError_t launch_shade(const DevScene& sc, const DevFrame& fr, const DevParams
 }
 
 cudaError_t launch_shadow(const DevScene& sc, const DevFrame& fr, const DevParams& P, const Wave& w, int cur,
-                          int64_t max_n, int32_t* err, int sms, cudaStream_t st, const Job* jobs, bool wide) {
+                          int64_t max_n, int32_t* err, int sms, cudaStream_t st, const Job* jobs, int trav) {
     MCEV_TRAV_DISPATCH(k_shadow, grid_for(max_n, MCEV_TRAV_BLOCK, sms, 16), sc, fr, P, w, cur, err);
     return cudaGetLastError();
 }
 
 cudaError_t launch_shadow_extend(const DevScene& sc, const DevFrame& fr, const DevParams& P, const Wave& w, int cur,
-                                 int64_t max_n, int32_t* err, int sms, cudaStream_t st, const Job* jobs, bool wide) {
+                                 int64_t max_n, int32_t* err, int sms, cudaStream_t st, const Job* jobs, int trav) {
     const int g = grid_for(max_n, MCEV_TRAV_BLOCK, sms, 16);
     MCEV_TRAV_DISPATCH(k_shadow_extend, 2 * g, sc, fr, P, w, cur, g, err);
     return cudaGetLastError();

@@ -62,15 +62,20 @@ cudaError_t launch_raygen(const DevFrame& fr, const DevParams& P, const Wave& w,
                           int32_t spp_r, int64_t k_base, int64_t n_paths, int cur, int sms, cudaStream_t st,
                           const Job* jobs, const RoundCtl* rc = nullptr);
 // `wide`: the scenes' BLAS use the compressed 8-wide layout (Node8)
+// Traversal kernel variant (the `trav` argument of the launchers): the BLAS
+// layout, and whether the frame has two or more moving instances under a
+// TLAS (frames with at most one run kernels without the TLAS loop).
+enum { TRAV_WIDE = 1, TRAV_TLAS = 2 };
+
 cudaError_t launch_extend(const DevScene& sc, const DevFrame& fr, float t_min, const Wave& w, int cur, int64_t max_n,
-                          int32_t* err, int sms, cudaStream_t st, const Job* jobs, bool wide);
+                          int32_t* err, int sms, cudaStream_t st, const Job* jobs, int trav);
 cudaError_t launch_shade(const DevScene& sc, const DevFrame& fr, const DevParams& P, const Wave& w, int cur,
                          int64_t max_n, int sms, cudaStream_t st, const Job* jobs);
 cudaError_t launch_shadow(const DevScene& sc, const DevFrame& fr, const DevParams& P, const Wave& w, int cur,
-                          int64_t max_n, int32_t* err, int sms, cudaStream_t st, const Job* jobs, bool wide);
+                          int64_t max_n, int32_t* err, int sms, cudaStream_t st, const Job* jobs, int trav);
 // shadow rays of the bounce with queue `cur` and closest hits of queue 1 - cur, in one launch
 cudaError_t launch_shadow_extend(const DevScene& sc, const DevFrame& fr, const DevParams& P, const Wave& w, int cur,
-                                 int64_t max_n, int32_t* err, int sms, cudaStream_t st, const Job* jobs, bool wide);
+                                 int64_t max_n, int32_t* err, int sms, cudaStream_t st, const Job* jobs, int trav);
 cudaError_t launch_stats(const Wave& w, const StatsArgs& A, const int32_t* queue, int64_t j0, int64_t n_pix,
                          int32_t* next_queue, int sms, cudaStream_t st, const Job* jobs, const RoundCtl* rc = nullptr);
 // device-resident round loop: start state (and, with iota, queue 0 = 0..Q0-1)

@@ -301,12 +301,13 @@ def cornell_box(seed: int = 20240815, shift: float = 0.02) -> Scene:
 
 def icosphere_field(seed: int = 20240816, n_spheres: int = 64, level: int = 4,
                     n_frames: int = 33, dt: float = 1.0e-3, spin_hz: float = 1.0,
-                    env_w: int = 512, env_h: int = 256) -> Scene:
+                    env_w: int = 512, env_h: int = 256, n_spin: int = 1) -> Scene:
     """64 icospheres (subdivision `level`, 20*4^level triangles each) with a
     radial vertex displacement ~U(0, 0.05), seed-placed on a 2-triangle
-    ground plane.  All surfaces Lambertian with albedo ~U(0.2, 0.9).  Sphere 0
-    spins about its vertical axis at `spin_hz` turns per second; keyframes at
-    k*dt for k < n_frames.  Lit by the procedural sky."""
+    ground plane.  All surfaces Lambertian with albedo ~U(0.2, 0.9).  Spheres
+    s < n_spin spin about their vertical axes, sphere s at spin_hz * (1 + s/4)
+    turns per second (default: sphere 0 alone); keyframes at k*dt for
+    k < n_frames.  Lit by the procedural sky."""
     rng = np.random.default_rng(seed)
     base_v, base_f = _icosphere(level)
     mb = _MeshBuilder()
@@ -341,7 +342,7 @@ def icosphere_field(seed: int = 20240816, n_spheres: int = 64, level: int = 4,
     xf = np.zeros((n_frames, ni, 12))
     for k, tk in enumerate(times):
         for s in range(n_spheres):
-            rot = 2.0 * math.pi * spin_hz * tk if s == 0 else 0.0
+            rot = 2.0 * math.pi * spin_hz * (1.0 + s / 4.0) * tk if s < n_spin else 0.0
             xf[k, s] = _affine(1.0, rot, (positions[s][0], radii[s], positions[s][1]))
         xf[k, n_spheres] = IDENTITY
     eye = np.broadcast_to([0.0, 7.5, 11.0], (n_frames, 3))

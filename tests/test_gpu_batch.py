@@ -19,7 +19,9 @@ SCHED = tuple(SCHEDULE.values())    # positional: (C, alpha, spp_batch, spp_max)
 
 def _jobs():
     c = sg.workload("cornell64")
-    small = sg.icosphere_field(7, n_spheres=6, level=3, n_frames=3, dt=5e-3, env_w=64, env_h=32)
+    # three spinning spheres: a TLAS in the job's frames, so the batch runs the
+    # traversal variant with the TLAS loop for every job
+    small = sg.icosphere_field(7, n_spheres=6, level=3, n_frames=3, dt=5e-3, env_w=64, env_h=32, n_spin=3)
     ws = [
         (c.scene, 64, 64, c),
         (c.scene, 40, 24, c),

@@ -20,7 +20,7 @@ KEYS = ("events", "spp", "mean")
 
 
 def _small_spheres():
-    sc = sg.icosphere_field(7, n_spheres=6, level=3, n_frames=4, dt=5e-3, env_w=64, env_h=32)
+    sc = sg.icosphere_field(7, n_spheres=6, level=3, n_frames=4, dt=5e-3, env_w=64, env_h=32, n_spin=3)
     return sg.Workload("spheres_small", sc, 96, 64, [0.0, 1.0, 2.0, 3.0], spp_min=16, spp_batch=16, spp_max=512,
                        C=0.2, alpha=0.05, max_depth=4, seed=7, t_min=2e-4)
 
