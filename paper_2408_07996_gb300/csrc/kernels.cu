@@ -25,8 +25,9 @@ namespace mcev {
 // blocks of 128 threads cap them at 56 registers (56% occupancy); traversal
 // waits on node fetches, so more resident warps pay more than the few
 // registers spilled (terrain frame traversal: 72 registers 1011 ms, 64
-// registers 967 ms, 56 registers 943 ms, 48 registers 961 ms).  0 leaves the
-// choice to the compiler.
+// registers 967 ms, 56 registers 943 ms, 48 registers 961 ms; whole terrain
+// frames with the kernels that carry no TLAS code: 64 / 56 / 48 registers
+// 1332 / 1289 / 1306 ms).  0 leaves the choice to the compiler.
 #ifndef MCEV_TRAV_MINB
 #define MCEV_TRAV_MINB 9
 #endif
