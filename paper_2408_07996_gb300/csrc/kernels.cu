@@ -635,6 +635,16 @@ __global__ void k_iota(int32_t* q, int64_t n) {
 }
 
 // ------------------------------------------------------------------ launchers
+// Traversal grids: up to 72 blocks of 128 threads per SM (8 waves of the 9
+// resident blocks), each thread striding over the ray queue.  Per-ray
+// traversal cost is heavy-tailed, and smaller per-block shares let the block
+// scheduler even out the SMs' ends (terrain frame: 16 / 36 / 72 / 144 blocks
+// per SM 1286 / 1245 / 1239 / 1261 ms; one ray per thread with no cap
+// 1992 ms, the empty blocks of late, small rounds costing more).
+#ifndef MCEV_TRAV_BLOCKS_PER_SM
+#define MCEV_TRAV_BLOCKS_PER_SM 72
+#endif
+
 static int grid_for(int64_t work, int block, int sms, int per_sm) {
     int64_t g = (work + block - 1) / block;
     const int64_t cap = (int64_t)sms * per_sm;
@@ -676,7 +686,8 @@ cudaError_t launch_raygen(const DevFrame& fr, const DevParams& P, const Wave& w,
 
 cudaError_t launch_extend(const DevScene& sc, const DevFrame& fr, float t_min, const Wave& w, int cur, int64_t max_n,
                           int32_t* err, int sms, cudaStream_t st, const Job* jobs, int trav) {
-    MCEV_TRAV_DISPATCH(k_extend, grid_for(max_n, MCEV_TRAV_BLOCK, sms, 16), sc, fr, t_min, w, cur, err);
+    MCEV_TRAV_DISPATCH(k_extend, grid_for(max_n, MCEV_TRAV_BLOCK, sms, MCEV_TRAV_BLOCKS_PER_SM), sc, fr, t_min, w, cur,
+                       err);
     return cudaGetLastError();
 }
 
@@ -691,13 +702,14 @@ cudaError_t launch_shade(const DevScene& sc, const DevFrame& fr, const DevParams
 
 cudaError_t launch_shadow(const DevScene& sc, const DevFrame& fr, const DevParams& P, const Wave& w, int cur,
                           int64_t max_n, int32_t* err, int sms, cudaStream_t st, const Job* jobs, int trav) {
-    MCEV_TRAV_DISPATCH(k_shadow, grid_for(max_n, MCEV_TRAV_BLOCK, sms, 16), sc, fr, P, w, cur, err);
+    MCEV_TRAV_DISPATCH(k_shadow, grid_for(max_n, MCEV_TRAV_BLOCK, sms, MCEV_TRAV_BLOCKS_PER_SM), sc, fr, P, w, cur,
+                       err);
     return cudaGetLastError();
 }
 
 cudaError_t launch_shadow_extend(const DevScene& sc, const DevFrame& fr, const DevParams& P, const Wave& w, int cur,
                                  int64_t max_n, int32_t* err, int sms, cudaStream_t st, const Job* jobs, int trav) {
-    const int g = grid_for(max_n, MCEV_TRAV_BLOCK, sms, 16);
+    const int g = grid_for(max_n, MCEV_TRAV_BLOCK, sms, MCEV_TRAV_BLOCKS_PER_SM);
     MCEV_TRAV_DISPATCH(k_shadow_extend, 2 * g, sc, fr, P, w, cur, g, err);
     return cudaGetLastError();
 }
