@@ -329,10 +329,10 @@ QUALITY_BYTES_PER_EVENT = 4
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per traced ray of
 # the traversal launches (k_extend + k_shadow_extend, two-wide BVH), from a
-# one-pass ncu capture of every launch of one timed terrain frame (315.7 GB
+# one-pass ncu capture of every launch of one timed terrain frame (315.2 GB
 # over 294 launches that traced 3.852 G closest-hit and shadow rays); set to
 # None when the traversal kernels change.
-TRAVERSAL_DRAM_BYTES_PER_RAY = 81.96
+TRAVERSAL_DRAM_BYTES_PER_RAY = 81.82
 
 
 def traversal_traffic(rays_per_launch: float, bvh_width: int = 2):

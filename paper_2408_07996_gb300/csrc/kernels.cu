@@ -104,17 +104,58 @@ __global__ void __launch_bounds__(256) k_raygen(DevFrame fr, DevParams P, Wave w
 // traversal work counters: 64-bit (nodes, tris) pairs after the int32
 // counters, and the ray/box tests (two per node fetch of the two-wide BVH)
 enum { WORK_CLOSEST = 0, WORK_SHADOW = 1 };
+// Per-block accumulation of the traversal work counters: work_begin at the
+// top of a ray loop (every thread of the block), add_work after it.  Each
+// warp adds its sums in shared memory; the last warp of the block to finish
+// adds the block's totals to the global counters (skipped when the block
+// traced nothing), so a launch's global atomics on these three words scale
+// with its busy blocks, not with its warps, and no warp waits for another.
+struct WorkAcc {
+    unsigned long long v[3];
+    unsigned int done;
+};
+
+__device__ __forceinline__ WorkAcc& work_acc() {
+    __shared__ WorkAcc acc;
+    return acc;
+}
+
+__device__ __forceinline__ void work_begin() {
+    WorkAcc& a = work_acc();
+    if (threadIdx.x == 0) {
+        a.v[0] = a.v[1] = a.v[2] = 0ull;
+        a.done = 0u;
+    }
+    __syncthreads();
+}
+
 template <bool kWide>
 __device__ __forceinline__ void add_work(const Wave& w, int which, int3 work) {
-    const unsigned m = __activemask();
+    WorkAcc& a = work_acc();
+    // the whole warp, reconverged after its ray loop: one count per warp
+    __syncwarp();
+    const unsigned m = 0xffffffffu;
     const int nodes = __reduce_add_sync(m, work.x);
     const int tris = __reduce_add_sync(m, work.y);
     const int boxes = kWide ? __reduce_add_sync(m, work.z) : 2 * nodes;
-    if ((threadIdx.x & 31) == (__ffs(m) - 1)) {
-        unsigned long long* c = reinterpret_cast<unsigned long long*>(w.counters + 32);
-        atomicAdd(c + 2 * which, (unsigned long long)nodes);
-        atomicAdd(c + 2 * which + 1, (unsigned long long)tris);
-        atomicAdd(c + 7 + which, (unsigned long long)boxes);
+    if ((threadIdx.x & 31) == 0) {
+        if (nodes | tris) {
+            atomicAdd(&a.v[0], (unsigned long long)nodes);
+            atomicAdd(&a.v[1], (unsigned long long)tris);
+            atomicAdd(&a.v[2], (unsigned long long)boxes);
+        }
+        __threadfence_block();
+        if (atomicAdd(&a.done, 1u) == (blockDim.x >> 5) - 1u) {
+            __threadfence_block();
+            const unsigned long long n0 = atomicAdd(&a.v[0], 0ull), n1 = atomicAdd(&a.v[1], 0ull),
+                                     n2 = atomicAdd(&a.v[2], 0ull);
+            if (n0 | n1) {
+                unsigned long long* c = reinterpret_cast<unsigned long long*>(w.counters + 32);
+                atomicAdd(c + 2 * which, n0);
+                atomicAdd(c + 2 * which + 1, n1);
+                atomicAdd(c + 7 + which, n2);
+            }
+        }
     }
 }
 
@@ -134,6 +175,7 @@ __device__ __forceinline__ void extend_rays(const DevScene& sc, const DevFrame& 
     }
     int e = 0;
     int3 work = make_int3(0, 0, 0);
+    work_begin();
     for (int64_t i = first; i < n; i += stride) {
         const float4 o = w.ray_o[cur][i];
         const float4 d = w.ray_d[cur][i];
@@ -395,6 +437,7 @@ __device__ __forceinline__ void shadow_rays(const DevScene& sc, const DevFrame& 
     if (first == 0) atomicAdd(reinterpret_cast<unsigned long long*>(w.counters + 32) + 5, (unsigned long long)n);
     int e = 0;
     int3 work = make_int3(0, 0, 0);
+    work_begin();
     for (int64_t i = first; i < n; i += stride) {
         const float4 o = w.sh_o[i];
         const float4 d = w.sh_d[i];
