@@ -139,6 +139,29 @@ def test_bvh_matches_brute_force_instanced_spheres():
     assert hits > 10
 
 
+def test_bvh_matches_brute_force_many_moving_instances():
+    # eight of twelve spheres spin (the moving-instance parity scene's kind),
+    # at times between and on keyframes, so the oracle's per-frame instance
+    # transforms are exercised for several instances at once
+    sc = sg.icosphere_field(11, n_spheres=12, level=3, n_frames=4, dt=0.05, env_w=64, env_h=32, n_spin=8)
+    moving = [s for s in range(12) if not np.allclose(sc.inst_xform[0, s], sc.inst_xform[-1, s])]
+    assert moving == list(range(8))
+    osc = O.OracleScene(sc)
+    rng = np.random.default_rng(22)
+    hits = set()
+    for i in range(400):
+        o = np.array([rng.uniform(-7, 7), rng.uniform(2, 4), rng.uniform(-7, 7)])
+        d = np.array([rng.uniform(-0.3, 0.3), -1.0, rng.uniform(-0.3, 0.3)])
+        d /= np.linalg.norm(d)
+        t = [0.0, 0.05, 0.075, 0.1][i % 4]
+        a = osc.closest_hit(t, o, d, 1e-4, np.inf, True)
+        b = osc.closest_hit(t, o, d, 1e-4, np.inf, False)
+        assert a == b
+        if a[0] and a[2] < 8:
+            hits.add(a[2])
+    assert len(hits) >= 3
+
+
 def test_watertight_shared_edge():
     # rays aimed at points of the shared diagonal of a split quad never leak
     osc = O.OracleScene(sg.plane_under_env(0.5, 1.0, half=1.0))
